@@ -1,0 +1,418 @@
+"""Benchmark of the fused eps-chain forward + VJP (Eq. 1) on GB300.
+
+One step = one fused forward + VJP call (eps_vjp with eps_out) on the
+600 x 600-control / 300 x 300 x 24 Yee workload (R = 6, beta = 16, one
+wavelength of complex64 E_F and E_A), i.e. every stage of the chain: filter,
+projection, mixing, dual-cell means, Sobel normals, Eq. 7, the eps_hat
+write, the Eq. 1 field contraction and the adjoint scatter to dJ/dC.
+
+Timing: W warm-up steps, then exactly K steps.  Before every step a 256 MB
+buffer is zeroed on the same stream (L2 flush); CUDA events bracket each
+call and exclude the flush.  value = design voxels (nx ny nz) per second of
+summed call time; with torchrun every rank runs its own region (weak
+scaling) and the slowest rank's time is used.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import datetime as _dt
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "design voxels/s for fused eps-chain forward+VJP"
+UNIT = "voxels/s"
+L2_FLUSH_BYTES = 256 << 20
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SOURCES = ["paper_2505_03352_gb300/csrc/epsc_fwd.cuh",
+                  "paper_2505_03352_gb300/csrc/epsc_common.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self, wait_s: float = 5.0):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        t0 = time.time()
+        while not self.samples and time.time() - t0 < wait_s:
+            time.sleep(0.05)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = _dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                sm = float(parts[2])
+                smax = float(parts[3])
+            except ValueError:
+                continue
+            flags = dict(zip(self.REASONS, [p.lower() == "active" for p in parts[6:10]]))
+            self.samples.append((ts, sm, smax, flags))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        inside = [s for s in self.samples if t0 - 0.05 <= s[0] <= t1 + 0.15]
+        use = inside or sorted(self.samples, key=lambda s: abs(s[0] - (t0 + t1) / 2))[:3]
+        reasons = sorted({r for s in use for r, on in s[3].items() if on})
+        return {"sm_mhz": statistics.median(s[1] for s in use),
+                "sm_max_mhz": max(s[2] for s in use), "reasons": reasons,
+                "samples": len(use), "in_timed_region": bool(inside)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def committed_traffic(workload: str):
+    """dram read+write bytes per launch of the dominant kernel from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    with open(PROFILE_TRAFFIC) as f:
+        d = json.load(f)
+    ent = d.get(workload)
+    if not ent or ent.get("kernel_hash") != kernel_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def algorithmic_bytes(w, n_lambda):
+    """Bytes the fused forward/contraction kernel must move: C read, eps_hat
+    write and the J-support field planes (3 nk + 1 planes of E_F and E_A, 8 B
+    each, per Yee column and wavelength)."""
+    cols = w.nx * w.ny
+    planes = 3 * w.slab_nk + 1
+    return 4 * w.mx * w.my + 12 * cols * w.nz + cols * n_lambda * planes * 2 * 8
+
+
+def cpu_baseline(w, budget_s: float = 15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import numpy as np
+    from oracle import epschain_oracle as orc
+    from paper_2505_03352_gb300 import synth
+    C = synth.controls(w)
+    EF, EA = synth.fields(w)
+    op = orc.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        orc.eps_hat(op, C)
+        orc.vjp_fields(op, C, EF, EA)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 20:
+            break
+    dt = time.perf_counter() - t0
+    del np
+    return {"value": reps * w.voxels / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full forward+VJP calls of {w.name} (numpy float64, single thread)",
+            "seconds": round(dt, 2)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import paper_2505_03352_gb300 as ec
+    from paper_2505_03352_gb300 import synth
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = synth.WORKLOADS[2]
+    prob = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+    C = synth.controls(w)
+    EF, EA = synth.fields(w)
+    Cd = torch.from_numpy(C).to(dev)
+    EFd = [torch.from_numpy(e).to(dev) for e in EF]
+    EAd = [torch.from_numpy(e).to(dev) for e in EA]
+    dJdC = torch.empty((w.mx, w.my), dtype=torch.float32, device=dev)
+    eps = torch.empty((3, w.nx, w.ny, w.nz), dtype=torch.float32, device=dev)
+    call = ec.PreparedVjp(prob, Cd, EFd, EAd, dJdC, eps_out=eps)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also fills the library's event pool)
+    ec.eps_profile_start()
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        call()
+    torch.cuda.synchronize()
+    ec.eps_profile_stop(64)
+    ec.eps_sync_status()
+
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",")]
+        if local < len(ids) and ids[local].isdigit():
+            gpu_index = int(ids[local])
+    sampler = ClockSampler(gpu_index).start() if rank == 0 else None
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    barrier()
+    ec.eps_profile_start()
+    t0 = time.time()
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record(stream)
+        call()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    prof = ec.eps_profile_stop(64)
+    barrier()
+    ec.eps_sync_status()
+    ms_total = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    time.sleep(0.25)
+    clocks = None
+    if sampler is not None:
+        sampler.stop()
+        clocks = sampler.summary(t0, t1)
+
+    ms_step = ms_total / K
+    value = world * w.voxels * K / (ms_total * 1e-3)
+
+    # dominant kernel roofline (forward + contraction), events from the library
+    fwd_name = "eps_fwd_vjp_contract"
+    n_f, t_f = prof.get(fwd_name, (0, 0.0))
+    n_b, t_b = prof.get("eps_vjp_scatter", (0, 0.0))
+    peak, peak_kind = measured_peaks()
+    alg = algorithmic_bytes(w, 1)
+    f_ms = t_f / max(n_f, 1)
+    achieved = alg / (f_ms * 1e-3) / 1e9
+    traffic = committed_traffic(w.name)
+    roofline = {"bound": "hbm", "kernel": fwd_name, "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(f_ms, 5),
+                "scatter_avg_launch_ms": round(t_b / max(n_b, 1), 5)}
+
+    # end to end: pinned host buffers, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        hC = torch.from_numpy(C).pin_memory()
+        hEF = [torch.from_numpy(e).pin_memory() for e in EF]
+        hEA = [torch.from_numpy(e).pin_memory() for e in EA]
+        hG = torch.empty((w.mx, w.my), dtype=torch.float32).pin_memory()
+        hE = torch.empty((3, w.nx, w.ny, w.nz), dtype=torch.float32).pin_memory()
+        h2d = hC.numel() * 4 + sum(t.numel() * 8 for t in hEF + hEA)
+        d2h = hG.numel() * 4 + hE.numel() * 4
+
+        def e2e_step():
+            Cd.copy_(hC, non_blocking=True)
+            for d, h in zip(EFd + EAd, hEF + hEA):
+                d.copy_(h, non_blocking=True)
+            call()
+            hG.copy_(dJdC, non_blocking=True)
+            hE.copy_(eps, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        e2e = {"value": world * w.voxels * args.e2e_steps / (ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": round(ms / args.e2e_steps, 4),
+               "path": "pinned host -> device copies, eps_vjp, device -> host copies, one stream"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "controls": [w.mx, w.my],
+                       "yee": [w.nx, w.ny, w.nz], "radius_px": w.radius, "beta": w.beta,
+                       "eta": w.eta, "wavelengths": 1, "fields": "complex64",
+                       "slab_planes": w.slab_nk, "bc": "clamp",
+                       "l2": "256 MB buffer zeroed before every step, outside the timed events",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": n_f + n_b,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    del np
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world):
+    """The FP64 oracle, as it stands, on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from oracle import epschain_oracle as orc
+    from paper_2505_03352_gb300 import synth
+    w = synth.WORKLOADS[2]
+    C = synth.controls(w)
+    EF, EA = synth.fields(w)
+    op = orc.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+
+    def step(win):
+        sl = (slice(0, win), slice(0, win))
+        c = C[sl]
+        ef = [e[:, : win // 2, : win // 2, :] for e in EF]
+        ea = [e[:, : win // 2, : win // 2, :] for e in EA]
+        p = orc.Problem(mx=win, my=win, nz=w.nz, radius=w.radius, beta=w.beta)
+        orc.eps_hat(p, c)
+        orc.vjp_fields(p, c, ef, ea)
+        return (win // 2) ** 2 * w.nz
+
+    # size the per-step sample so warm-up + steps stay within about two minutes
+    t0 = time.perf_counter()
+    step(w.mx)
+    full = time.perf_counter() - t0
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    win = w.mx
+    if full > budget:
+        win = max(64, int(w.mx * (budget / full) ** 0.5) // 2 * 2)
+    for _ in range(args.warmup):
+        step(win)
+    t0 = time.perf_counter()
+    vox = 0
+    for _ in range(args.steps):
+        vox += step(win)
+    dt = time.perf_counter() - t0
+    value = vox / dt
+    sample = (f"{win} x {win}-control window of {w.name} per step "
+              f"({(win // 2) ** 2 * w.nz} voxels), numpy float64, single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / max(args.steps, 1) * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "controls": [w.mx, w.my], "yee": [w.nx, w.ny, w.nz],
+                   "radius_px": w.radius, "beta": w.beta, "wavelengths": 1,
+                   "fields": "complex64", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

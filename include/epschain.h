@@ -1,0 +1,179 @@
+/*
+ * epschain — GB300 (sm_103a) library for the differentiable map from
+ * topology-optimisation control variables C to the subpixel-smoothed
+ * anisotropic permittivity eps_hat on an FDTD Yee grid, and its adjoint.
+ *
+ * Method: Sofronov, Yakovleva, Yakubovich, "Accelerated inverse design of
+ * passive Si photonics" (arXiv 2505.03352).
+ *   - density mixing and 2-D mask extruded in z ............. Sec. 3, par. 1
+ *   - filter (conic basis, Eq. 2) and tanh projection ........ Eq. 2, 3, 6
+ *   - per-component dual-cell means, half-cell shift ......... Eq. 8, Sec. 3
+ *   - Sobel normals and anisotropic smoothing ................ Eq. 7, Sec. 3
+ *   - vector-Jacobian product without forming J .............. Sec. 3 (end)
+ *   - adjoint gradient dJ/dC = -2 Re(deps/dC . (E_F E_A)) .... Eq. 1 + footnote
+ *
+ * Conventions shared by every entry point:
+ *   * Layouts are C order.  C and dJ/dC are float32 [mx][my] (controls at
+ *     pitch d, `sub` = 2 subpixels per Yee cell per in-plane axis, so the Yee
+ *     grid is nx = mx/2 by ny = my/2 by nz).  eps_hat and real cotangents G
+ *     are float32 [3][nx][ny][nz] (component xx, yy, zz; z fastest).  Fields
+ *     are complex64 [3][nx][ny][nz] with interleaved (re, im), one array per
+ *     wavelength; only the planes where eps_hat depends on C are read.
+ *   * Every pointer marked "device" is device memory owned by the caller.
+ *     The library never allocates device memory inside a call; scratch space
+ *     is the caller's workspace, sized by eps_workspace_size().
+ *   * Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream).  Argument errors return before any launch, with
+ *     nothing written.  Launch failures return EPS_ERR_CUDA.  Device-side
+ *     error flags are reported by eps_sync_status().
+ *   * Calls on different streams are independent and may run concurrently
+ *     when each has its own workspace.
+ */
+#ifndef EPSCHAIN_H
+#define EPSCHAIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *eps_stream_t;
+
+typedef enum {
+  EPS_OK = 0,
+  EPS_ERR_INVALID_ARG = 1,   /* null pointer, bad enum, non-finite parameter */
+  EPS_ERR_SHAPE = 2,         /* sizes inconsistent or out of range */
+  EPS_ERR_WORKSPACE = 3,     /* workspace null, misaligned or too small */
+  EPS_ERR_UNSUPPORTED = 4,   /* valid request outside what is built (sub != 2, radius > max) */
+  EPS_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+  EPS_ERR_DEVICE_TIMEOUT = 6,/* a bounded device-side wait gave up */
+  EPS_ERR_DEVICE_BOUNDS = 7  /* a device-side bounds check fired (debug builds) */
+} eps_status_t;
+
+typedef enum { EPS_BC_CLAMP = 0, EPS_BC_PERIODIC = 1 } eps_bc_t;
+
+typedef enum {
+  EPS_FIELD_C64 = 0,          /* complex64 [3][nx][ny][nz] */
+  EPS_FIELD_BF16X2_SCALED = 1,/* bf16 (re, im) pairs, slab planes only; see eps_field_pack */
+  EPS_FIELD_F16X2_SCALED = 2  /* fp16 (re, im) pairs, slab planes only; see eps_field_pack */
+} eps_field_t;
+
+/* flags */
+#define EPS_FLAG_OFFDIAG 1  /* eps_forward also writes the xy inverse-permittivity term */
+
+#define EPS_MAX_LAMBDA 16    /* wavelengths per eps_vjp call */
+#define EPS_MAX_RADIUS 12.0f /* largest conic filter radius (subpixels) */
+
+/*
+ * One design region.  Eq. 2 / 3 / 6 / 7 parameters plus the slab geometry.
+ *   mx, my     control grid, both even, 2 <= mx, my
+ *   sub        subpixels per Yee cell per in-plane axis; must be 2
+ *   nz         Yee cells along z
+ *   slab_k0    lower Ez face plane of the slab; -1 picks (nz - nk - 1) / 2.
+ *              Faces sit at z = (k0 + 1/2) D and (k0 + nk + 1/2) D, so
+ *              Ex/Ey planes k0+1 .. k0+nk and Ez planes k0+1 .. k0+nk-1 lie
+ *              in the slab and Ez planes k0, k0+nk straddle its faces.
+ *              Requires 0 <= k0 and k0 + nk <= nz - 1.
+ *   slab_nk    slab thickness in Yee cells, >= 1
+ *   radius     conic filter radius R in subpixels, 0 < R <= EPS_MAX_RADIUS;
+ *              taps at integer offsets with r < R, weight (1 - r/R)/sum
+ *   beta, eta  projection rho = (1 + tanh(beta (u - eta))) / 2
+ *   eps_core, eps_clad  permittivities mixed by rho (Sec. 3)
+ *   bc         eps_bc_t: edge rule for the filter, the dual cells and Sobel
+ *   flags      EPS_FLAG_*
+ */
+typedef struct {
+  int32_t mx, my, sub, nz, slab_k0, slab_nk;
+  float radius, beta, eta, eps_core, eps_clad;
+  int32_t bc, flags;
+} eps_problem_t;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *eps_status_string(eps_status_t status);
+
+/*
+ * Workspace bytes eps_vjp / eps_vjp_real need for `prob` (n_lambda is
+ * accepted for forward compatibility; the size does not depend on it).
+ * Workspace pointers must be 256-byte aligned.
+ */
+eps_status_t eps_workspace_size(const eps_problem_t *prob, int32_t n_lambda, size_t *bytes);
+
+/*
+ * Forward chain (Eq. 2 -> 6 -> mixing -> Eq. 8 -> Sobel normals -> Eq. 7):
+ *   C        device, float32 [mx][my]
+ *   eps      device, float32 [3][nx][ny][nz], written in full (cladding
+ *            planes get eps_clad)
+ *   offdiag  device, float32 [2][nx][ny][nz] or NULL; written only when
+ *            flags has EPS_FLAG_OFFDIAG: n_x n_y (<1/eps> - 1/<eps>) at the
+ *            Ex points (index 0) and Ey points (index 1) on the slab planes,
+ *            0 elsewhere.  Forward only: Eq. 1 uses zero off-diagonals.
+ */
+eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps,
+                         float *offdiag, eps_stream_t stream);
+
+/*
+ * Adjoint gradient, Eq. 1:  dJdC = (d eps_hat / dC)^T W,
+ *   W = scale * Re( sum_l  s_l * E_F,l (.) E_A,l ),  elementwise and
+ *   unconjugated (Eq. 1 footnote), scale = -2 for d|alpha|^2/dC.
+ *   n_lambda      1 .. EPS_MAX_LAMBDA wavelengths (host count)
+ *   field_type    eps_field_t of EF / EA
+ *   EF, EA        host arrays of n_lambda device pointers, each 16-byte
+ *                 aligned.  C64: complex64 [3][nx][ny][nz] (nz even).
+ *                 Packed types: the layout eps_field_pack writes.
+ *   field_scales  host float [n_lambda][2][3] (wavelength, field F/A,
+ *                 component) multiplying each stored component, or NULL
+ *                 for all ones; required for the packed types
+ *   dJdC          device, float32 [mx][my], overwritten
+ *   eps_out       device float32 [3][nx][ny][nz] or NULL; when given the
+ *                 forward eps_hat is written by the same pass (fused
+ *                 forward + VJP)
+ *   ws, ws_bytes  device workspace of at least eps_workspace_size() bytes
+ * The filtered density and projection are recomputed from C; nothing from
+ * an earlier eps_forward is reused.
+ */
+eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda,
+                     int32_t field_type, const void *const *EF, const void *const *EA,
+                     const float *field_scales, float scale, float *dJdC, float *eps_out,
+                     void *ws, size_t ws_bytes, eps_stream_t stream);
+
+/*
+ * Vector-Jacobian product for an arbitrary real cotangent (Sec. 3, end):
+ *   dJdC = (d eps_hat / dC)^T G,   G device float32 [3][nx][ny][nz].
+ * Used by autograd backward passes; recomputes the forward from C.
+ */
+eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float *G,
+                          float *dJdC, void *ws, size_t ws_bytes, eps_stream_t stream);
+
+/*
+ * Synchronise `stream`, then return (and clear) any device-side error flag
+ * raised by earlier calls on this device: EPS_ERR_DEVICE_TIMEOUT or
+ * EPS_ERR_DEVICE_BOUNDS, else EPS_OK; EPS_ERR_CUDA if the sync failed.
+ */
+eps_status_t eps_sync_status(eps_stream_t stream);
+
+/*
+ * Per-kernel timing.  While enabled, each launch made by this library is
+ * bracketed by CUDA events on its stream.  eps_profile_stop() waits for the
+ * recorded events and fills up to max_entries records (kernel name, number
+ * of launches, summed milliseconds); *n_entries gets the number written.
+ * Host-side state is process-global: do not profile from several host
+ * threads at once.
+ */
+typedef struct {
+  char name[48];
+  int32_t launches;
+  double total_ms;
+} eps_profile_entry_t;
+
+eps_status_t eps_profile_start(void);
+eps_status_t eps_profile_stop(eps_profile_entry_t *entries, int32_t max_entries,
+                              int32_t *n_entries);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPSCHAIN_H */

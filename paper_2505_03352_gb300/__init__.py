@@ -1,0 +1,20 @@
+"""GB300 (sm_103a) library for the differentiable control-variables ->
+Yee-grid permittivity chain of arXiv 2505.03352 and its Eq. 1 adjoint.
+
+The CUDA kernels live in csrc/ behind the C ABI of include/epschain.h;
+`epschain` is the thin ctypes binding (same function names), `autograd`
+wraps it as torch.autograd.Functions, `synth` draws the seeded inputs.
+"""
+
+from .epschain import (EPS_BC_CLAMP, EPS_BC_PERIODIC, EPS_FIELD_C64, EPS_FIELD_BF16X2_SCALED,
+                       EPS_FIELD_F16X2_SCALED, EPS_FLAG_OFFDIAG, EpsError, PreparedVjp, Problem,
+                       eps_forward,
+                       eps_profile_start, eps_profile_stop, eps_status_string, eps_sync_status,
+                       eps_vjp, eps_vjp_real, eps_workspace_size, lib)
+
+__all__ = [
+    "EPS_BC_CLAMP", "EPS_BC_PERIODIC", "EPS_FIELD_C64", "EPS_FIELD_BF16X2_SCALED",
+    "EPS_FIELD_F16X2_SCALED", "EPS_FLAG_OFFDIAG", "EpsError", "PreparedVjp", "Problem", "eps_forward",
+    "eps_profile_start", "eps_profile_stop", "eps_status_string", "eps_sync_status", "eps_vjp",
+    "eps_vjp_real", "eps_workspace_size", "lib",
+]

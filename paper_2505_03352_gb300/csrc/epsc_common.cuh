@@ -1,0 +1,152 @@
+// Shared definitions of the epschain CUDA kernels (sm_103a).
+//
+// Tiling.  The forward pass works on tiles of TI x TJ Yee columns (x rows,
+// y contiguous), one thread per column in the per-column stages.  The
+// backward scatter works on tiles of TA x TB control subpixels.  Both use
+// 256-thread blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "epschain.h"
+
+namespace epsc {
+
+constexpr int NTHREADS = 256;
+
+// forward tile (Yee cells) and its subpixel region
+constexpr int TI = 8;
+constexpr int TJ = 32;
+constexpr int UA = 2 * TI + 5;   // subpixel rows a in [2 i0 - 3, 2 i0 + 2 TI + 1]
+constexpr int UB = 2 * TJ + 5;   // subpixel cols b in [2 j0 - 3, 2 j0 + 2 TJ + 1]
+constexpr int NA_F = 7;          // filter outputs per thread (rows of a strip)
+static_assert(UA % NA_F == 0, "forward strips must tile the subpixel rows");
+
+// backward tile (subpixels)
+constexpr int TA = 32;
+constexpr int TB = 64;
+constexpr int NA_B = 8;
+
+// filter radius limit: RP1 = ceil(R) taps per half-axis including the centre
+constexpr int MAX_RP1 = 12;
+constexpr int MAX_BOX = 2 * MAX_RP1 - 1;
+
+// |g|^2 threshold below which the interface normal is undefined (m = 0)
+constexpr float NORMAL_TAU2 = 1e-12f;
+
+enum Mode : int { MODE_FWD = 0, MODE_C64 = 1, MODE_REAL = 2 };
+
+// seed planes written by the forward/contraction kernel, [NSEED][nx][ny]
+enum Seed : int {
+  S_DAX = 0, S_DHX, S_GXX, S_GYX,   // x: dJ/dA_x, dJ/dH_x, dJ/dg_x(U_x), dJ/dg_y(U_x)
+  S_DAY, S_DHY, S_GXY, S_GYY,       // y: same for U_y
+  S_DAZ, S_DHZ,                     // z: dJ/dA_z, dJ/dH_z
+  NSEED
+};
+
+struct Geometry {
+  int mx, my, nx, ny, nz, k0, nk, bc;
+  float beta, eta, eps_core, eps_clad, deps;
+};
+
+struct FwdArgs {
+  Geometry g;
+  int mode;
+  int write_eps;
+  int write_offdiag;
+  int nlambda;
+  const float *C;
+  float *eps;
+  float *offdiag;
+  const float *G;
+  float *seeds;
+  float *uws;
+  int *err;
+  const float4 *EF[EPS_MAX_LAMBDA];
+  const float4 *EA[EPS_MAX_LAMBDA];
+  float fs[EPS_MAX_LAMBDA][3];   // scale * s_F * s_A per wavelength and component
+  float w[MAX_BOX * MAX_BOX];    // conic weights, dense (2 RP1 - 1)^2 box, row-major
+};
+
+struct BwdArgs {
+  Geometry g;
+  const float *seeds;
+  const float *uws;
+  float *dJdC;
+  int *err;
+  float w[MAX_BOX * MAX_BOX];
+};
+
+__device__ __forceinline__ int clampi(int x, int lo, int hi) { return min(max(x, lo), hi); }
+
+__device__ __forceinline__ int wrapi(int x, int n) {
+  int r = x % n;
+  return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ int bc_map(int x, int n, int bc) {
+  return bc == EPS_BC_CLAMP ? clampi(x, 0, n - 1) : wrapi(x, n);
+}
+
+// Knuth's TwoSum: hi + lo += x with the rounding error of the add kept in lo.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (x - bb);
+  hi = s;
+  lo += err;
+}
+
+// Register-blocked conic stencil over a strip of NA outputs stacked along the
+// row direction.  `src` points at the input element that lies R rows above and
+// R columns left of output 0; output k is
+//     sum_{p,q} w[(p+R)(2R+1) + q+R] * src[(k + p + R) * pitch + q + R].
+// Every input row is read once from shared memory and reused by all NA
+// outputs.  With COMP the per-row partial sums are accumulated with TwoSum
+// (hi + lo), which keeps u accurate to about one ulp where the projection
+// amplifies its error by up to beta/2.
+template <int RP1, int NA, bool COMP, class Args>
+__device__ __forceinline__ void strip_stencil(const float *__restrict__ src, int pitch,
+                                              const Args &a, float (&hi)[NA], float (&lo)[NA]) {
+  constexpr int R = RP1 - 1;
+  constexpr int BW = 2 * R + 1;
+#pragma unroll
+  for (int k = 0; k < NA; ++k) {
+    hi[k] = 0.f;
+    lo[k] = 0.f;
+  }
+#pragma unroll
+  for (int rr = 0; rr < NA + 2 * R; ++rr) {
+    float v[BW];
+#pragma unroll
+    for (int q = 0; q < BW; ++q) v[q] = src[rr * pitch + q];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      const int p = rr - k - R;
+      if (p >= -R && p <= R) {
+        float part = 0.f;
+#pragma unroll
+        for (int q = -R; q <= R; ++q) {
+          if (p * p + q * q < RP1 * RP1) part = fmaf(a.w[(p + R) * BW + q + R], v[q + R], part);
+        }
+        if (COMP)
+          two_sum_acc(hi[k], lo[k], part);
+        else
+          hi[k] += part;
+      }
+    }
+  }
+}
+
+// Fast unsigned division by a runtime divisor d for small numerators:
+// q = umulhi(n, m) with m = ceil(2^32 / d) is exact whenever n * d^2 < 2^32
+// (the rounding excess of m is below d, so n * excess / 2^32 < 1 / d).
+struct FastDiv {
+  unsigned d, m;
+  __device__ __forceinline__ explicit FastDiv(unsigned d_)
+      : d(d_), m(d_ > 1u ? 0xFFFFFFFFu / d_ + 1u : 0u) {}
+  __device__ __forceinline__ unsigned div(unsigned n) const { return d == 1u ? n : __umulhi(n, m); }
+};
+
+}  // namespace epsc

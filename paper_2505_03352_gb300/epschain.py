@@ -1,0 +1,299 @@
+"""Python binding of the epschain C ABI (include/epschain.h).
+
+Argument marshalling only: every step of the chain runs in the CUDA kernels
+of libepschain.so.  PyTorch supplies device memory and streams.  The
+functions carry the names of the C entry points; they raise EpsError on any
+status other than EPS_OK.  There is no CPU fallback: without the built
+library every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libepschain.so")
+
+EPS_OK = 0
+STATUS_NAMES = {
+    0: "EPS_OK", 1: "EPS_ERR_INVALID_ARG", 2: "EPS_ERR_SHAPE", 3: "EPS_ERR_WORKSPACE",
+    4: "EPS_ERR_UNSUPPORTED", 5: "EPS_ERR_CUDA", 6: "EPS_ERR_DEVICE_TIMEOUT",
+    7: "EPS_ERR_DEVICE_BOUNDS",
+}
+EPS_BC_CLAMP, EPS_BC_PERIODIC = 0, 1
+EPS_FIELD_C64, EPS_FIELD_BF16X2_SCALED, EPS_FIELD_F16X2_SCALED = 0, 1, 2
+EPS_FLAG_OFFDIAG = 1
+EPS_MAX_LAMBDA = 16
+
+
+class EpsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+
+
+class eps_problem_t(ctypes.Structure):
+    _fields_ = [
+        ("mx", ctypes.c_int32), ("my", ctypes.c_int32), ("sub", ctypes.c_int32),
+        ("nz", ctypes.c_int32), ("slab_k0", ctypes.c_int32), ("slab_nk", ctypes.c_int32),
+        ("radius", ctypes.c_float), ("beta", ctypes.c_float), ("eta", ctypes.c_float),
+        ("eps_core", ctypes.c_float), ("eps_clad", ctypes.c_float),
+        ("bc", ctypes.c_int32), ("flags", ctypes.c_int32),
+    ]
+
+
+class eps_profile_entry_t(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int32),
+                ("total_ms", ctypes.c_double)]
+
+
+@dataclass(frozen=True)
+class Problem:
+    """Mirror of eps_problem_t (see include/epschain.h for the meaning)."""
+
+    mx: int
+    my: int
+    nz: int
+    radius: float
+    beta: float
+    eta: float = 0.5
+    eps_core: float = 12.11
+    eps_clad: float = 2.085
+    slab_nk: int = 11
+    slab_k0: int = -1
+    bc: int = EPS_BC_CLAMP
+    flags: int = 0
+    sub: int = 2
+
+    @property
+    def nx(self):
+        return self.mx // self.sub
+
+    @property
+    def ny(self):
+        return self.my // self.sub
+
+    @property
+    def k0(self):
+        return self.slab_k0 if self.slab_k0 >= 0 else (self.nz - self.slab_nk - 1) // 2
+
+    def c_struct(self) -> eps_problem_t:
+        return eps_problem_t(self.mx, self.my, self.sub, self.nz, self.slab_k0, self.slab_nk,
+                             self.radius, self.beta, self.eta, self.eps_core, self.eps_clad,
+                             self.bc, self.flags)
+
+
+_lib = None
+
+_VP = ctypes.c_void_p
+_PROTOS = {
+    "eps_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "eps_workspace_size": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_size_t)]),
+    "eps_forward": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP]),
+    "eps_vjp": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, ctypes.c_int32, ctypes.c_int32,
+                               _VP, _VP, _VP, ctypes.c_float, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "eps_vjp_real": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP,
+                                    ctypes.c_size_t, _VP]),
+    "eps_sync_status": (ctypes.c_int, [_VP]),
+    "eps_profile_start": (ctypes.c_int, []),
+    "eps_profile_stop": (ctypes.c_int, [ctypes.POINTER(eps_profile_entry_t), ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32)]),
+}
+
+
+def lib():
+    """The loaded libepschain.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2505_03352_gb300.build_lib`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _PROTOS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != EPS_OK:
+        raise EpsError(status, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t, shape, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def eps_status_string(status: int) -> str:
+    return lib().eps_status_string(status).decode()
+
+
+def eps_workspace_size(prob: Problem, n_lambda: int = 1) -> int:
+    n = ctypes.c_size_t(0)
+    p = prob.c_struct()
+    _check(lib().eps_workspace_size(ctypes.byref(p), n_lambda, ctypes.byref(n)),
+           "eps_workspace_size")
+    return n.value
+
+
+def eps_forward(prob: Problem, C, eps=None, offdiag=None, stream=None):
+    """eps_hat [3, nx, ny, nz] float32 (and the off-diagonal term when
+    prob.flags has EPS_FLAG_OFFDIAG).  Returns eps, or (eps, offdiag)."""
+    import torch
+    _need(C, (prob.mx, prob.my), torch.float32, "C")
+    shape = (3, prob.nx, prob.ny, prob.nz)
+    if eps is None:
+        eps = torch.empty(shape, dtype=torch.float32, device=C.device)
+    _need(eps, shape, torch.float32, "eps")
+    want_od = bool(prob.flags & EPS_FLAG_OFFDIAG)
+    if want_od and offdiag is None:
+        offdiag = torch.empty((2,) + shape[1:], dtype=torch.float32, device=C.device)
+    p = prob.c_struct()
+    _check(lib().eps_forward(ctypes.byref(p), _ptr(C), _ptr(eps), _ptr(offdiag) if want_od else None,
+                             _stream(stream)), "eps_forward")
+    return (eps, offdiag) if want_od else eps
+
+
+def _workspace(prob, n_lambda, ws, device):
+    import torch
+    need = eps_workspace_size(prob, n_lambda)
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
+    return ws
+
+
+def eps_vjp(prob: Problem, C, EF, EA, scale: float = -2.0, dJdC=None, eps_out=None,
+            field_type: int = EPS_FIELD_C64, field_scales=None, ws=None, stream=None):
+    """Eq. 1 adjoint gradient dJ/dC [mx, my] from lists of forward / adjoint
+    field tensors (complex64 [3, nx, ny, nz] for EPS_FIELD_C64).  With
+    eps_out (a tensor, or True to allocate one) the forward eps_hat is
+    written by the same pass.  Returns dJdC, or (dJdC, eps_out)."""
+    import torch
+    _need(C, (prob.mx, prob.my), torch.float32, "C")
+    if len(EF) != len(EA):
+        raise ValueError("EF and EA must have the same number of wavelengths")
+    nl = len(EF)
+    if nl > EPS_MAX_LAMBDA:
+        raise ValueError(f"at most {EPS_MAX_LAMBDA} wavelengths per call")
+    if field_type == EPS_FIELD_C64:
+        for l in range(nl):
+            _need(EF[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EF[{l}]")
+            _need(EA[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EA[{l}]")
+    if dJdC is None:
+        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=C.device)
+    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC")
+    ret_eps = eps_out is not None and eps_out is not False
+    if eps_out is True:
+        eps_out = torch.empty((3, prob.nx, prob.ny, prob.nz), dtype=torch.float32, device=C.device)
+    if ret_eps:
+        _need(eps_out, (3, prob.nx, prob.ny, prob.nz), torch.float32, "eps_out")
+    ws = _workspace(prob, nl, ws, C.device)
+    ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
+    ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
+    fs = None
+    if field_scales is not None:
+        flat = [float(v) for v in _flatten(field_scales)]
+        if len(flat) != 6 * nl:
+            raise ValueError("field_scales must hold n_lambda x 2 x 3 values")
+        fs = (ctypes.c_float * len(flat))(*flat)
+    p = prob.c_struct()
+    _check(lib().eps_vjp(ctypes.byref(p), _ptr(C), nl, field_type, ef, ea, fs, float(scale),
+                         _ptr(dJdC), _ptr(eps_out) if ret_eps else None, _ptr(ws), ws.numel(),
+                         _stream(stream)), "eps_vjp")
+    return (dJdC, eps_out) if ret_eps else dJdC
+
+
+def _flatten(x):
+    if hasattr(x, "tolist"):
+        x = x.tolist()
+    if isinstance(x, (list, tuple)):
+        out = []
+        for v in x:
+            out.extend(_flatten(v))
+        return out
+    return [x]
+
+
+def eps_vjp_real(prob: Problem, C, G, dJdC=None, ws=None, stream=None):
+    """(d eps_hat / dC)^T G for a real float32 cotangent G [3, nx, ny, nz]."""
+    import torch
+    _need(C, (prob.mx, prob.my), torch.float32, "C")
+    _need(G, (3, prob.nx, prob.ny, prob.nz), torch.float32, "G")
+    if dJdC is None:
+        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=C.device)
+    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC")
+    ws = _workspace(prob, 1, ws, C.device)
+    p = prob.c_struct()
+    _check(lib().eps_vjp_real(ctypes.byref(p), _ptr(C), _ptr(G), _ptr(dJdC), _ptr(ws), ws.numel(),
+                              _stream(stream)), "eps_vjp_real")
+    return dJdC
+
+
+def eps_sync_status(stream=None):
+    _check(lib().eps_sync_status(_stream(stream)), "eps_sync_status")
+
+
+def eps_profile_start():
+    _check(lib().eps_profile_start(), "eps_profile_start")
+
+
+def eps_profile_stop(max_entries: int = 32):
+    """{kernel name: (launches, total_ms)} for launches since eps_profile_start."""
+    arr = (eps_profile_entry_t * max_entries)()
+    n = ctypes.c_int32(0)
+    _check(lib().eps_profile_stop(arr, max_entries, ctypes.byref(n)), "eps_profile_stop")
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n.value)}
+
+
+class PreparedVjp:
+    """A fused forward + VJP call (eps_vjp) with its ctypes arguments built
+    once, for launch loops where per-call marshalling would dominate.  The
+    tensors passed in are kept alive by this object; calling it launches on
+    `stream` (default: the current stream) and raises on a bad status."""
+
+    def __init__(self, prob: Problem, C, EF, EA, dJdC, eps_out=None, ws=None, scale=-2.0,
+                 field_type: int = EPS_FIELD_C64, field_scales=None):
+        nl = len(EF)
+        self._keep = (C, list(EF), list(EA), dJdC, eps_out)
+        if ws is None:
+            ws = _workspace(prob, nl, None, C.device)
+        self._ws = ws
+        self._p = prob.c_struct()
+        self._ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
+        self._ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
+        self._fs = None
+        if field_scales is not None:
+            flat = [float(v) for v in _flatten(field_scales)]
+            self._fs = (ctypes.c_float * len(flat))(*flat)
+        self._args = (ctypes.byref(self._p), _ptr(C), nl, field_type, self._ef, self._ea, self._fs,
+                      float(scale), _ptr(dJdC), _ptr(eps_out), _ptr(ws), ws.numel())
+        self._fn = lib().eps_vjp
+
+    def __call__(self, stream=None):
+        _check(self._fn(*self._args, _stream(stream)), "eps_vjp")

@@ -1,0 +1,219 @@
+"""GPU (CUDA path, through the C ABI) vs the FP64 oracle, element by element.
+
+Tolerances (FP32 path, beta <= 32):
+  eps_hat:  max |gpu - ref| / |ref|            <= 1e-5
+  dJ/dC:    max |gpu - ref| / max |ref|        <= 1e-4
+"""
+
+import numpy as np
+import pytest
+
+from oracle import epschain_oracle as orc
+from paper_2505_03352_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+EPS_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ec():
+    import paper_2505_03352_gb300 as ec
+    return ec
+
+
+def eps_err(got, ref):
+    return float(np.max(np.abs(got - ref) / np.abs(ref)))
+
+
+def grad_err(got, ref):
+    scale = np.max(np.abs(ref))
+    if scale == 0:
+        return float(np.max(np.abs(got)))
+    return float(np.max(np.abs(got - ref)) / scale)
+
+
+def problems(mx, my, nz, radius, beta, bc=0, slab_k0=-1, slab_nk=11, eta=0.5, flags=0):
+    ec = _ec()
+    p = ec.Problem(mx=mx, my=my, nz=nz, radius=radius, beta=beta, bc=bc, slab_k0=slab_k0,
+                   slab_nk=slab_nk, eta=eta, flags=flags)
+    o = orc.Problem(mx=mx, my=my, nz=nz, radius=radius, beta=beta, bc=bc, slab_k0=slab_k0,
+                    slab_nk=slab_nk, eta=eta)
+    return p, o
+
+
+def to_dev(x):
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run_vjp(p, C, EF, EA, field_scales=None, eps_out=True):
+    ec = _ec()
+    out = ec.eps_vjp(p, to_dev(C), [to_dev(e) for e in EF], [to_dev(e) for e in EA],
+                     eps_out=eps_out, field_scales=field_scales)
+    ec.eps_sync_status()
+    if eps_out:
+        return out[0].cpu().numpy(), out[1].cpu().numpy()
+    return out.cpu().numpy(), None
+
+
+def check_case(p, o, C, EF, EA, field_scales=None):
+    g, e = run_vjp(p, C, EF, EA, field_scales=field_scales)
+    ref = orc.forward(o, C)["eps_hat"]
+    ref_g = orc.vjp_fields(o, C, EF, EA, field_scales=field_scales)
+    assert eps_err(e, ref) <= EPS_TOL, eps_err(e, ref)
+    assert grad_err(g, ref_g) <= GRAD_TOL, grad_err(g, ref_g)
+    # the forward-only entry point gives the same eps_hat
+    ec = _ec()
+    e2 = ec.eps_forward(p, to_dev(C)).cpu().numpy()
+    ec.eps_sync_status()
+    assert eps_err(e2, ref) <= EPS_TOL
+
+
+def test_cfg1_fused_forward_vjp():
+    w = synth.WORKLOADS[1]
+    p, o = problems(w.mx, w.my, w.nz, w.radius, w.beta)
+    C = synth.controls(w)
+    EF, EA = synth.fields(w)
+    check_case(p, o, C, EF, EA)
+
+
+def test_cfg2_full_size_elementwise():
+    w = synth.WORKLOADS[2]
+    p, o = problems(w.mx, w.my, w.nz, w.radius, w.beta)
+    C = synth.controls(w)
+    EF, EA = synth.fields(w)
+    check_case(p, o, C, EF, EA)
+
+
+CASES = [
+    # mx, my, nz, R, beta, bc
+    (70, 134, 16, 3.0, 8.0, 0),
+    (70, 134, 16, 3.0, 8.0, 1),
+    (66, 130, 24, 6.0, 16.0, 0),
+    (66, 130, 24, 6.0, 16.0, 1),
+    (96, 64, 24, 8.0, 32.0, 0),
+    (96, 64, 24, 8.0, 32.0, 1),
+    (34, 98, 14, 2.5, 4.0, 0),
+    (34, 98, 14, 1.0, 32.0, 1),
+    (18, 66, 16, 11.5, 16.0, 0),
+    (130, 18, 16, 0.5, 8.0, 1),
+    (8, 8, 14, 2.0, 8.0, 0),
+    (8, 8, 14, 2.0, 8.0, 1),
+    (2, 6, 14, 3.0, 8.0, 0),
+    (6, 2, 14, 3.0, 8.0, 1),
+    (4, 4, 14, 6.0, 32.0, 1),
+]
+
+
+@pytest.mark.parametrize("mx,my,nz,radius,beta,bc", CASES)
+def test_random_shapes_match_oracle(mx, my, nz, radius, beta, bc):
+    p, o = problems(mx, my, nz, radius, beta, bc)
+    rng = np.random.default_rng(mx * 1000 + my + int(radius * 10) + bc)
+    C = rng.random((mx, my), dtype=np.float32)
+    shape = (3, p.nx, p.ny, nz)
+    EF = [synth.complex_field(shape, 77 + mx)]
+    EA = [synth.complex_field(shape, 78 + my)]
+    check_case(p, o, C, EF, EA)
+
+
+@pytest.mark.parametrize("beta", [4.0, 8.0, 16.0, 32.0])
+def test_soi_layout_all_betas(beta):
+    p, o = problems(160, 224, 24, 6.0, beta)
+    C = synth.soi_layout(160, 224, 55)
+    shape = (3, p.nx, p.ny, 24)
+    EF = [synth.complex_field(shape, 5)]
+    EA = [synth.complex_field(shape, 6)]
+    check_case(p, o, C, EF, EA)
+
+
+def test_multi_wavelength_with_field_scales():
+    p, o = problems(64, 96, 16, 3.0, 8.0)
+    rng = np.random.default_rng(3)
+    C = rng.random((64, 96), dtype=np.float32)
+    shape = (3, p.nx, p.ny, 16)
+    EF = [synth.complex_field(shape, 10 + l) for l in range(3)]
+    EA = [synth.complex_field(shape, 20 + l) for l in range(3)]
+    fs = rng.uniform(0.5, 2.0, size=(3, 2, 3)).astype(np.float32)
+    check_case(p, o, C, EF, EA, field_scales=fs)
+
+
+def test_custom_slab_position_and_thickness():
+    p, o = problems(48, 64, 20, 3.0, 8.0, slab_k0=1, slab_nk=7)
+    rng = np.random.default_rng(4)
+    C = rng.random((48, 64), dtype=np.float32)
+    shape = (3, p.nx, p.ny, 20)
+    check_case(p, o, C, [synth.complex_field(shape, 1)], [synth.complex_field(shape, 2)])
+
+
+def test_vjp_real_cotangent():
+    ec = _ec()
+    p, o = problems(70, 134, 18, 6.0, 16.0, bc=1)
+    rng = np.random.default_rng(5)
+    C = rng.random((70, 134), dtype=np.float32)
+    G = rng.standard_normal((3, p.nx, p.ny, 18)).astype(np.float32)
+    g = ec.eps_vjp_real(p, to_dev(C), to_dev(G)).cpu().numpy()
+    ec.eps_sync_status()
+    ref = orc.vjp_real(o, C, G)
+    assert grad_err(g, ref) <= GRAD_TOL
+
+
+def test_vjp_real_odd_nz():
+    ec = _ec()
+    p, o = problems(40, 72, 15, 3.0, 8.0)
+    rng = np.random.default_rng(6)
+    C = rng.random((40, 72), dtype=np.float32)
+    G = rng.standard_normal((3, p.nx, p.ny, 15)).astype(np.float32)
+    g = ec.eps_vjp_real(p, to_dev(C), to_dev(G)).cpu().numpy()
+    e = ec.eps_forward(p, to_dev(C)).cpu().numpy()
+    ec.eps_sync_status()
+    assert grad_err(g, orc.vjp_real(o, C, G)) <= GRAD_TOL
+    assert eps_err(e, orc.eps_hat(o, C)) <= EPS_TOL
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_offdiagonal_forward(bc):
+    ec = _ec()
+    p, o = problems(70, 98, 16, 3.0, 8.0, bc=bc, flags=ec.EPS_FLAG_OFFDIAG)
+    rng = np.random.default_rng(7)
+    C = rng.random((70, 98), dtype=np.float32)
+    eps, od = ec.eps_forward(p, to_dev(C))
+    ec.eps_sync_status()
+    ref = orc.forward(o, C, offdiag=True)
+    assert eps_err(eps.cpu().numpy(), ref["eps_hat"]) <= EPS_TOL
+    # off-diagonal entries cross zero: error relative to the largest entry
+    assert grad_err(od.cpu().numpy(), ref["offdiag"]) <= 1e-4
+
+
+def test_uniform_design_is_uniform_on_gpu():
+    ec = _ec()
+    p, o = problems(64, 64, 16, 3.0, 8.0, bc=1)
+    C = np.full((64, 64), 0.5, np.float32)
+    e = ec.eps_forward(p, to_dev(C)).cpu().numpy()
+    ec.eps_sync_status()
+    np.testing.assert_allclose(e[0, :, :, p.k0 + 1], 0.5 * (12.11 + 2.085), rtol=1e-6)
+
+
+def test_zero_wavelengths_gives_zero_gradient():
+    ec = _ec()
+    torch = _torch()
+    p, _ = problems(32, 64, 16, 3.0, 8.0)
+    C = to_dev(np.random.default_rng(8).random((32, 64), dtype=np.float32))
+    g = ec.eps_vjp(p, C, [], [])
+    ec.eps_sync_status()
+    assert torch.count_nonzero(g).item() == 0
+
+
+def test_empty_region_is_a_no_op():
+    ec = _ec()
+    torch = _torch()
+    p = ec.Problem(mx=0, my=64, nz=16, radius=3.0, beta=8.0)
+    C = torch.empty((0, 64), dtype=torch.float32, device="cuda")
+    e = ec.eps_forward(p, C)
+    assert e.numel() == 0
+    ec.eps_sync_status()
