@@ -155,6 +155,17 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
 eps_status_t eps_sync_status(eps_stream_t stream);
 
 /*
+ * Set the L2 fetch granularity hint (cudaLimitMaxL2FetchGranularity, 0 ..
+ * 128 bytes) of the calling thread's current CUDA context and return the
+ * previous value in *previous (may be NULL).  The field reads of eps_vjp
+ * touch 32-byte sectors scattered at the column pitch, so a 32-byte
+ * granularity avoids DRAM fetches of the cladding planes between them.  The
+ * setting belongs to the context: it lasts until changed or until the
+ * process ends, and applies to every kernel in that context.
+ */
+eps_status_t eps_set_l2_fetch_granularity(int32_t bytes, int32_t *previous);
+
+/*
  * Per-kernel timing.  While enabled, each launch made by this library is
  * bracketed by CUDA events on its stream.  eps_profile_stop() waits for the
  * recorded events and fills up to max_entries records (kernel name, number

@@ -9,12 +9,14 @@ wraps it as torch.autograd.Functions, `synth` draws the seeded inputs.
 from .epschain import (EPS_BC_CLAMP, EPS_BC_PERIODIC, EPS_FIELD_C64, EPS_FIELD_BF16X2_SCALED,
                        EPS_FIELD_F16X2_SCALED, EPS_FLAG_OFFDIAG, EpsError, PreparedVjp, Problem,
                        eps_forward,
-                       eps_profile_start, eps_profile_stop, eps_status_string, eps_sync_status,
+                       eps_profile_start, eps_profile_stop, eps_set_l2_fetch_granularity,
+                       eps_status_string, eps_sync_status,
                        eps_vjp, eps_vjp_real, eps_workspace_size, lib)
 
 __all__ = [
     "EPS_BC_CLAMP", "EPS_BC_PERIODIC", "EPS_FIELD_C64", "EPS_FIELD_BF16X2_SCALED",
     "EPS_FIELD_F16X2_SCALED", "EPS_FLAG_OFFDIAG", "EpsError", "PreparedVjp", "Problem", "eps_forward",
-    "eps_profile_start", "eps_profile_stop", "eps_status_string", "eps_sync_status", "eps_vjp",
+    "eps_profile_start", "eps_profile_stop", "eps_set_l2_fetch_granularity", "eps_status_string",
+    "eps_sync_status", "eps_vjp",
     "eps_vjp_real", "eps_workspace_size", "lib",
 ]

@@ -3,6 +3,7 @@
 // error returns before any launch.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <set>
@@ -10,6 +11,10 @@
 #include <vector>
 
 #include "epschain.h"
+#include <cuda.h>
+
+#include "epsc_contract.cuh"
+#include "epsc_contract_tma.cuh"
 #include "epsc_launch.h"
 
 using namespace epsc;
@@ -82,10 +87,25 @@ eps_status_t resolve(const eps_problem_t *p, Resolved *r) {
   return EPS_OK;
 }
 
-size_t workspace_bytes(const Geometry &g) {
-  return align256(sizeof(float) * NSEED * (size_t)g.nx * g.ny) +
-         align256(sizeof(float) * (size_t)g.mx * g.my);
+// Workspace: W [4][nx][ny] | seeds [NSEED][nx][ny] | pd4 [mx][my] | ie2 [mx][my],
+// each 256-byte aligned.
+struct WsLayout {
+  size_t w, seeds, pd4, ie2, total;
+};
+
+WsLayout ws_layout(const Geometry &g) {
+  WsLayout L;
+  const size_t cells = (size_t)g.nx * g.ny;
+  const size_t subs = (size_t)g.mx * g.my;
+  L.w = 0;
+  L.seeds = L.w + align256(sizeof(float) * 4 * cells);
+  L.pd4 = L.seeds + align256(sizeof(float) * NSEED * cells);
+  L.ie2 = L.pd4 + align256(sizeof(float) * subs);
+  L.total = L.ie2 + align256(sizeof(float) * subs);
+  return L;
 }
+
+size_t workspace_bytes(const Geometry &g) { return ws_layout(g).total; }
 
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
@@ -113,23 +133,49 @@ cudaEvent_t pool_event() {
 // --------------------------------------------------------------- launching
 std::mutex g_attr_mu;
 std::set<std::pair<int, const void *>> g_attr_done;
+int g_sm_count[64];
 
-eps_status_t prepare(const KernelEntry &k) {
-  if (!k.fn) return EPS_ERR_UNSUPPORTED;
+// Largest dynamic shared memory any launch of this library asks for.
+constexpr size_t MAX_DYN_SMEM = 200 * 1024;
+
+eps_status_t prepare(const void *fn, size_t smem) {
+  if (!fn) return EPS_ERR_UNSUPPORTED;
+  if (smem > MAX_DYN_SMEM) return EPS_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return EPS_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_attr_mu);
-  if (g_attr_done.count({dev, k.fn})) return EPS_OK;
-  if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem) !=
+  if (g_attr_done.count({dev, fn})) return EPS_OK;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAX_DYN_SMEM) !=
       cudaSuccess)
     return EPS_ERR_CUDA;
-  g_attr_done.insert({dev, k.fn});
+  g_attr_done.insert({dev, fn});
   return EPS_OK;
 }
 
-eps_status_t launch(const char *name, const KernelEntry &k, dim3 grid, void *args,
-                    cudaStream_t s) {
-  eps_status_t st = prepare(k);
+eps_status_t sm_count(int *n) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return EPS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (g_sm_count[dev] == 0 &&
+      cudaDeviceGetAttribute(&g_sm_count[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return EPS_ERR_CUDA;
+  *n = g_sm_count[dev];
+  return EPS_OK;
+}
+
+bool profiling() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_prof_on;
+}
+
+// Launch `fn` (one by-value argument struct) on stream s.  With `pdl` the
+// kernel may begin while the previous kernel in the stream is still running
+// (programmatic dependent launch); it must then wait on that grid
+// (griddepcontrol.wait) before reading its results.  While profiling, each
+// launch is bracketed by events and launched without overlap.
+eps_status_t launch(const char *name, const void *fn, dim3 grid, size_t smem, void *args,
+                    cudaStream_t s, bool pdl = false) {
+  eps_status_t st = prepare(fn, smem);
   if (st != EPS_OK) return st;
   ProfRec rec{name, nullptr, nullptr};
   bool prof = false;
@@ -142,9 +188,21 @@ eps_status_t launch(const char *name, const KernelEntry &k, dim3 grid, void *arg
     }
   }
   if (prof && cudaEventRecord(rec.e0, s) != cudaSuccess) return EPS_ERR_CUDA;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (pdl && !prof) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
   void *params[] = {args};
-  if (cudaLaunchKernel(k.fn, grid, dim3(NTHREADS), params, k.smem, s) != cudaSuccess)
-    return EPS_ERR_CUDA;
+  if (cudaLaunchKernelExC(&cfg, fn, params) != cudaSuccess) return EPS_ERR_CUDA;
   if (prof) {
     if (cudaEventRecord(rec.e1, s) != cudaSuccess) return EPS_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -161,6 +219,17 @@ eps_status_t error_flag_ptr(int **out) {
 dim3 fwd_grid(const Geometry &g) { return dim3((g.ny + TJ - 1) / TJ, (g.nx + TI - 1) / TI); }
 dim3 bwd_grid(const Geometry &g) { return dim3((g.my + TB - 1) / TB, (g.mx + TA - 1) / TA); }
 
+// Dynamic shared memory of a forward launch: the stencil buffers, grown to
+// stage all of the tile's eps_hat components (up to 3) for one round of bulk
+// stores when that fits the budget.
+size_t fwd_smem(const KernelEntry &k, const Geometry &g, int ncomp, int *stage_floats) {
+  const size_t comp_bytes = sizeof(float) * TI * TJ * (size_t)g.nz;
+  size_t want = std::max(k.smem, std::min<size_t>(ncomp, 3) * comp_bytes);
+  if (want > MAX_DYN_SMEM) want = std::max(k.smem, std::min(MAX_DYN_SMEM, comp_bytes));
+  *stage_floats = (int)(want / sizeof(float));
+  return want;
+}
+
 void fill_fwd_common(FwdArgs &fa, const Resolved &r, const float *C, int *err) {
   std::memset(&fa, 0, sizeof(fa));
   fa.g = r.g;
@@ -169,17 +238,122 @@ void fill_fwd_common(FwdArgs &fa, const Resolved &r, const float *C, int *err) {
   std::memcpy(fa.w, r.w, sizeof(fa.w));
 }
 
-eps_status_t run_scatter(const Resolved &r, const float *seeds, const float *uws, float *dJdC,
+// Persistent contraction grid: a few blocks per SM, so that the stencil
+// kernel launched behind it (programmatic dependent launch) finds room on
+// every SM and its compute overlaps the field stream.
+constexpr int CONTRACT_BLOCKS_PER_SM = 2;
+
+eps_status_t run_contract(const ContractArgs &ca, int lanes, cudaStream_t s) {
+  int nsm = 0;
+  eps_status_t st = sm_count(&nsm);
+  if (st != EPS_OK) return st;
+  const long ncol = (long)ca.nx * ca.ny;
+  const long per_block = (NTHREADS / lanes) * 2;   // columns per block per iteration
+  long blocks = (ncol + per_block - 1) / per_block;
+  int bps = CONTRACT_BLOCKS_PER_SM;
+  if (const char *e = std::getenv("EPSC_EXP_CBPS")) bps = std::atoi(e);   // EXPERIMENT
+  blocks = std::min<long>(blocks, (long)nsm * bps);
+  return launch(ca.mode == MODE_C64 ? "eps_vjp_contract" : "eps_vjp_real_contract",
+                contract_entry(lanes), dim3((unsigned)std::max<long>(blocks, 1)), 0,
+                (void *)&ca, s);
+}
+
+// cuTensorMapEncodeTiled, resolved through the runtime (no link to libcuda)
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled encode_tiled() {
+  static PFN_encodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_encodeTiled)p;
+  });
+  return fn;
+}
+
+// J-support window of a column in floats: the 32-byte sectors holding
+// planes k0 .. k0+nk (complex64, 8 bytes per plane).
+void support_window(const Geometry &g, int *x0, int *bx) {
+  const int lo = (2 * g.k0) & ~7;
+  const int hi = (2 * (g.k0 + g.nk + 1) + 7) & ~7;
+  *x0 = lo;
+  *bx = hi - lo;
+}
+
+// Contraction through bulk tensor copies; returns EPS_ERR_UNSUPPORTED when
+// the fields or the window do not fit its requirements (caller falls back).
+eps_status_t run_contract_tma(const Geometry &g, int n_lambda, const void *const *EF,
+                              const void *const *EA, const float (*fs)[3], float *Wm, int *err,
+                              cudaStream_t s) {
+  PFN_encodeTiled enc = encode_tiled();
+  if (!enc) return EPS_ERR_UNSUPPORTED;
+  int x0 = 0, bx = 0;
+  support_window(g, &x0, &bx);
+  if (bx > TMA_BX_MAX || (g.nz & 1)) return EPS_ERR_UNSUPPORTED;
+  static_assert(sizeof(ContractTmaArgs) < 32000, "kernel parameter space");
+  ContractTmaArgs *ta = new ContractTmaArgs;
+  std::memset(ta, 0, sizeof(*ta));
+  const long ncol = (long)g.nx * g.ny;
+  const size_t comp_bytes = (size_t)ncol * g.nz * 8;
+  for (int l = 0; l < n_lambda; ++l) {
+    for (int f = 0; f < 2; ++f) {
+      // (2 nz floats) x (columns) x (3 components)
+      cuuint64_t dims[3] = {(cuuint64_t)(2 * g.nz), (cuuint64_t)ncol, 3};
+      cuuint64_t strides[2] = {(cuuint64_t)g.nz * 8, (cuuint64_t)comp_bytes};
+      cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)TMA_BY, 3};
+      cuuint32_t es[3] = {1, 1, 1};
+      if (enc(&ta->maps[l * 2 + f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+              (void *)(f == 0 ? EF[l] : EA[l]), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        delete ta;
+        return EPS_ERR_UNSUPPORTED;
+      }
+    }
+    for (int c = 0; c < 3; ++c) ta->fs[l][c] = fs[l][c];
+  }
+  ta->W = Wm;
+  ta->err = err;
+  ta->nx = g.nx;
+  ta->ny = g.ny;
+  ta->k0 = g.k0;
+  ta->nk = g.nk;
+  ta->nlambda = n_lambda;
+  ta->x0 = x0;
+  ta->bx = bx;
+  int nsm = 0;
+  eps_status_t st = sm_count(&nsm);
+  if (st == EPS_OK) {
+    const long nchunks = (ncol + TMA_BY - 1) / TMA_BY;
+    const long blocks = std::max<long>(1, std::min<long>(nchunks, (long)nsm * CONTRACT_BLOCKS_PER_SM));
+    const size_t smem = (size_t)TMA_NSTAGE * 6 * TMA_BY * bx * 4 + 128;
+    st = launch("eps_vjp_contract", contract_tma_entry(), dim3((unsigned)blocks), smem, ta, s);
+  }
+  delete ta;
+  return st;
+}
+
+eps_status_t run_scatter(const Resolved &r, const float *seeds, const float *pd4, const float *ie2,
+                         float *dJdC,
                          int *err, cudaStream_t s) {
   BwdArgs ba;
   std::memset(&ba, 0, sizeof(ba));
   ba.g = r.g;
   ba.seeds = seeds;
-  ba.uws = uws;
+  ba.pd4 = pd4;
+  ba.ie2 = ie2;
   ba.dJdC = dJdC;
   ba.err = err;
   std::memcpy(ba.w, r.w, sizeof(ba.w));
-  return launch("eps_vjp_scatter", bwd_entry(r.rp1), bwd_grid(r.g), &ba, s);
+  const KernelEntry k = bwd_entry(r.rp1, r.g.bc);
+  return launch("eps_vjp_scatter", k.fn, bwd_grid(r.g), k.smem, &ba, s);
 }
 
 }  // namespace
@@ -229,7 +403,9 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps, 
   fa.write_offdiag = od ? 1 : 0;
   fa.eps = eps;
   fa.offdiag = od ? offdiag : nullptr;
-  return launch("eps_forward", fwd_entry(r.rp1), fwd_grid(r.g), &fa, (cudaStream_t)stream);
+  const KernelEntry k = fwd_entry(r.rp1, r.g.bc);
+  const size_t smem = fwd_smem(k, r.g, od ? 5 : 3, &fa.stage_floats);
+  return launch("eps_forward", k.fn, fwd_grid(r.g), smem, &fa, (cudaStream_t)stream);
 }
 
 eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda,
@@ -262,30 +438,57 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   int *err = nullptr;
   if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
 
-  float *seeds = (float *)ws;
-  float *uws = (float *)((char *)ws + align256(sizeof(float) * NSEED * (size_t)r.g.nx * r.g.ny));
+  const WsLayout L = ws_layout(r.g);
+  float *Wm = (float *)((char *)ws + L.w);
+  float *seeds = (float *)((char *)ws + L.seeds);
+  float *pd4 = (float *)((char *)ws + L.pd4);
+  float *ie2 = (float *)((char *)ws + L.ie2);
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // 1. Eq. 1 column sums (streaming over the J-support planes)
+  ContractArgs ca;
+  std::memset(&ca, 0, sizeof(ca));
+  ca.nx = r.g.nx;
+  ca.ny = r.g.ny;
+  ca.nz = r.g.nz;
+  ca.k0 = r.g.k0;
+  ca.nk = r.g.nk;
+  ca.nlambda = n_lambda;
+  ca.mode = MODE_C64;
+  ca.W = Wm;
+  bool sector_ok = (r.g.nz & 3) == 0;
+  for (int l = 0; l < n_lambda; ++l) {
+    ca.EF[l] = (const float *)EF[l];
+    ca.EA[l] = (const float *)EA[l];
+    sector_ok = sector_ok && aligned(EF[l], 32) && aligned(EA[l], 32);
+    for (int c = 0; c < 3; ++c) {
+      float sc = scale;
+      if (field_scales) sc *= field_scales[(l * 2 + 0) * 3 + c] * field_scales[(l * 2 + 1) * 3 + c];
+      ca.fs[l][c] = sc;
+    }
+  }
+  st = (n_lambda > 0) ? run_contract_tma(r.g, n_lambda, EF, EA, ca.fs, Wm, err, s)
+                      : EPS_ERR_UNSUPPORTED;
+  if (st == EPS_ERR_UNSUPPORTED) st = run_contract(ca, sector_ok ? 4 : 8, s);
+  if (st != EPS_OK) return st;
+
+  // 2. forward chain + seeds (overlaps the contraction until it needs W)
   FwdArgs fa;
   fill_fwd_common(fa, r, C, err);
   fa.mode = MODE_C64;
   fa.write_eps = eps_out ? 1 : 0;
   fa.eps = eps_out;
-  fa.nlambda = n_lambda;
+  fa.W = Wm;
   fa.seeds = seeds;
-  fa.uws = uws;
-  for (int l = 0; l < n_lambda; ++l) {
-    fa.EF[l] = (const float4 *)EF[l];
-    fa.EA[l] = (const float4 *)EA[l];
-    for (int c = 0; c < 3; ++c) {
-      float s = scale;
-      if (field_scales) s *= field_scales[(l * 2 + 0) * 3 + c] * field_scales[(l * 2 + 1) * 3 + c];
-      fa.fs[l][c] = s;
-    }
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  st = launch(eps_out ? "eps_fwd_vjp_contract" : "eps_vjp_contract", fwd_entry(r.rp1),
-              fwd_grid(r.g), &fa, s);
+  fa.pd4 = pd4;
+  fa.ie2 = ie2;
+  const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
+  const size_t smem = fwd_smem(kf, r.g, eps_out ? 3 : 0, &fa.stage_floats);
+  st = launch(eps_out ? "eps_fwd_vjp_stencil" : "eps_vjp_stencil", kf.fn, fwd_grid(r.g), smem,
+              &fa, s, true);
   if (st != EPS_OK) return st;
-  return run_scatter(r, seeds, uws, dJdC, err, s);
+  // 3. transposes down to dJ/dC
+  return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
 }
 
 eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float *G, float *dJdC,
@@ -299,18 +502,35 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
   if (!ws || !aligned(ws, 256) || ws_bytes < workspace_bytes(r.g)) return EPS_ERR_WORKSPACE;
   int *err = nullptr;
   if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
-  float *seeds = (float *)ws;
-  float *uws = (float *)((char *)ws + align256(sizeof(float) * NSEED * (size_t)r.g.nx * r.g.ny));
+  const WsLayout L = ws_layout(r.g);
+  float *Wm = (float *)((char *)ws + L.w);
+  float *seeds = (float *)((char *)ws + L.seeds);
+  float *pd4 = (float *)((char *)ws + L.pd4);
+  float *ie2 = (float *)((char *)ws + L.ie2);
+  cudaStream_t s = (cudaStream_t)stream;
+  ContractArgs ca;
+  std::memset(&ca, 0, sizeof(ca));
+  ca.nx = r.g.nx;
+  ca.ny = r.g.ny;
+  ca.nz = r.g.nz;
+  ca.k0 = r.g.k0;
+  ca.nk = r.g.nk;
+  ca.mode = MODE_REAL;
+  ca.G = G;
+  ca.W = Wm;
+  if ((st = run_contract(ca, 8, s)) != EPS_OK) return st;
   FwdArgs fa;
   fill_fwd_common(fa, r, C, err);
   fa.mode = MODE_REAL;
-  fa.G = G;
+  fa.W = Wm;
   fa.seeds = seeds;
-  fa.uws = uws;
-  cudaStream_t s = (cudaStream_t)stream;
-  st = launch("eps_vjp_real_contract", fwd_entry(r.rp1), fwd_grid(r.g), &fa, s);
+  fa.pd4 = pd4;
+  fa.ie2 = ie2;
+  const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
+  const size_t smem = fwd_smem(kf, r.g, 0, &fa.stage_floats);
+  st = launch("eps_vjp_real_stencil", kf.fn, fwd_grid(r.g), smem, &fa, s, true);
   if (st != EPS_OK) return st;
-  return run_scatter(r, seeds, uws, dJdC, err, s);
+  return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
 }
 
 eps_status_t eps_sync_status(eps_stream_t stream) {
@@ -321,7 +541,17 @@ eps_status_t eps_sync_status(eps_stream_t stream) {
   if (flag == 0) return EPS_OK;
   const int zero = 0;
   if (cudaMemcpyToSymbol(g_eps_error_flag, &zero, sizeof(int)) != cudaSuccess) return EPS_ERR_CUDA;
-  return flag == EPS_ERR_DEVICE_TIMEOUT ? EPS_ERR_DEVICE_TIMEOUT : EPS_ERR_DEVICE_BOUNDS;
+  return (flag & ERRFLAG_TIMEOUT) ? EPS_ERR_DEVICE_TIMEOUT : EPS_ERR_DEVICE_BOUNDS;
+}
+
+eps_status_t eps_set_l2_fetch_granularity(int32_t bytes, int32_t *previous) {
+  if (bytes < 0 || bytes > 128) return EPS_ERR_INVALID_ARG;
+  size_t old = 0;
+  if (cudaDeviceGetLimit(&old, cudaLimitMaxL2FetchGranularity) != cudaSuccess) return EPS_ERR_CUDA;
+  if (previous) *previous = (int32_t)old;
+  if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes) != cudaSuccess)
+    return EPS_ERR_CUDA;
+  return EPS_OK;
 }
 
 eps_status_t eps_profile_start(void) {

@@ -1,0 +1,15 @@
+// Instantiations of the Eq. 1 contraction kernel (4 lanes per column with
+// 32-byte sector loads, or 8 lanes per column with 16-byte loads).
+#include "epsc_contract.cuh"
+#include "epsc_contract_tma.cuh"
+#include "epsc_launch.h"
+
+namespace epsc {
+
+const void *contract_entry(int lanes) {
+  return lanes == 4 ? (const void *)&contract_kernel<4> : (const void *)&contract_kernel<8>;
+}
+
+const void *contract_tma_entry() { return (const void *)&contract_tma_kernel<TMA_NSTAGE>; }
+
+}  // namespace epsc

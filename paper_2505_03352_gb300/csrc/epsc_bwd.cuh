@@ -5,6 +5,10 @@
 //   ->  projection P'(u) (analytic, Eq. 6)  ->  K^T (Eq. 2).
 // Edge replicate is a many-to-one index map; its transpose folds every
 // contribution that landed outside the region back onto the edge element.
+//
+// Everything the tile needs (u, the seed maps of the touched cells and the
+// Sobel seeds with a one-cell halo) is staged into shared memory with
+// asynchronous copies first, so the global reads are all in flight at once.
 #pragma once
 
 #include "epsc_common.cuh"
@@ -21,69 +25,66 @@ struct BwdSmem {
   static constexpr int DBP = TB + 4 * R;                       // du pitch
   static constexpr int NCI = (TA + 4 * R) / 2 + 3;             // cell rows covering du
   static constexpr int NCJ = (TB + 4 * R) / 2 + 3;
-  static constexpr int OFF_DUX = 0;
-  static constexpr int OFF_DUY = OFF_DUX + NCI * NCJ;
-  static constexpr int OFF_DU = OFF_DUY + NCI * NCJ;
-  static constexpr int OFF_DCE = OFF_DU + DA_ALLOC * DBP;
+  static constexpr int NC = NCI * NCJ;
+  static constexpr int NGJ = NCJ + 2;                          // Sobel seeds: one-cell halo
+  static constexpr int NG = (NCI + 2) * NGJ;
+  static constexpr int OFF_U = 0;                              // P' deps / 4, then du in place
+  static constexpr int OFF_IE2 = OFF_U + DA_ALLOC * DBP;       // 1 / eps^2
+  static constexpr int OFF_SEED = OFF_IE2 + DA_ALLOC * DBP;    // 6 maps: dA, dH of x, y, z
+  static constexpr int OFF_G = OFF_SEED + 6 * NC;              // 4 maps: dg of U_x, U_y
+  static constexpr int OFF_DU = OFF_G + 4 * NG;                // 2 maps: dU_x, dU_y
+  static constexpr int OFF_DCE = OFF_DU + 2 * NC;
   static constexpr int TOTAL = OFF_DCE + GA_MAX * GB_MAX;
   static constexpr size_t BYTES = sizeof(float) * TOTAL;
 };
 
-// Transposed 3-tap Sobel factors along one axis: for target cell t, three
-// source cells s with weights wd = sum_{d: bc(s+d)=t} D(d) and
-// ws = sum_{d: bc(s+d)=t} S(d), D = (-1, 0, 1), S = (1, 2, 1).  Sources that
-// do not exist (edge replicate at the region edge) get zero weights.
-struct SobelT {
-  int src[3];
-  float wd[3], ws[3];
-};
-
-__device__ __forceinline__ SobelT sobel_t_axis(int t, int n, int bc) {
-  SobelT r;
-  if (bc == EPS_BC_PERIODIC) {
-    // each (s, d) with wrap(s + d) = t is s = wrap(t - d): one term per d
+// Transposed 3-tap Sobel weights along one axis for target cell t and the
+// sources s = t - 1 + e (e = 0, 1, 2):  wd = sum_{d: bc(s+d)=t} D(d),
+// ws = sum_{d: bc(s+d)=t} S(d), D = (-1, 0, 1), S = (1, 2, 1).  Under edge
+// replicate, sources outside [0, n) do not exist and get zero weights.
+__device__ __forceinline__ void sobel_t_weights(int t, int n, int bc, float (&wd)[3],
+                                                float (&ws)[3]) {
 #pragma unroll
-    for (int d = -1; d <= 1; ++d) {
-      r.src[d + 1] = wrapi(t - d, n);
-      r.wd[d + 1] = (float)d;
-      r.ws[d + 1] = d == 0 ? 2.f : 1.f;
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
+  for (int e = 0; e < 3; ++e) {
+    if (bc == EPS_BC_PERIODIC) {
+      const int d = 1 - e;   // the single offset with s + d = t
+      wd[e] = (float)d;
+      ws[e] = d == 0 ? 2.f : 1.f;
+    } else {
       const int s = t - 1 + e;
-      float wd = 0.f, ws = 0.f;
+      float a = 0.f, b = 0.f;
       if (s >= 0 && s < n) {
 #pragma unroll
         for (int d = -1; d <= 1; ++d) {
           if (clampi(s + d, 0, n - 1) == t) {
-            wd += (float)d;
-            ws += d == 0 ? 2.f : 1.f;
+            a += (float)d;
+            b += d == 0 ? 2.f : 1.f;
           }
         }
       }
-      r.src[e] = clampi(s, 0, n - 1);
-      r.wd[e] = wd;
-      r.ws[e] = ws;
+      wd[e] = a;
+      ws[e] = b;
     }
   }
-  return r;
 }
 
-template <int RP1>
+template <int RP1, int BC>
 __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ BwdArgs a) {
   using S = BwdSmem<RP1>;
   constexpr int R = S::R;
   constexpr int DBP = S::DBP;
-  extern __shared__ float smem[];
-  float *sdUx = smem + S::OFF_DUX;
-  float *sdUy = smem + S::OFF_DUY;
-  float *sdu = smem + S::OFF_DU;
+  constexpr bool clamp = BC == EPS_BC_CLAMP;
+  extern __shared__ __align__(16) float smem[];
+  float *sU = smem + S::OFF_U;
+  float *sIE2 = smem + S::OFF_IE2;
+  float *sSeed = smem + S::OFF_SEED;
+  float *sG = smem + S::OFF_G;
+  float *sdU = smem + S::OFF_DU;
   float *sdc = smem + S::OFF_DCE;
 
   const Geometry &g = a.g;
   const int tid = threadIdx.x;
-  const bool clamp = g.bc == EPS_BC_CLAMP;
+  const int ty = tid >> 5, tx = tid & 31;       // 8 x 32 thread grid for 2-D loops
   const int a0 = blockIdx.y * TA, b0 = blockIdx.x * TB;
   const int aend = min(a0 + TA, g.mx), bend = min(b0 + TB, g.my);
   // gather region: the tile, plus R extended positions where edge replicate folds
@@ -100,118 +101,156 @@ __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ B
   const int NCI = ((da_lo + DA) >> 1) - ci_lo + 1;
   const int NCJ = ((db_lo + DB) >> 1) - cj_lo + 1;
   const size_t plane = (size_t)g.nx * g.ny;
+  const int NSTRIP = (GA + NA_B - 1) / NA_B;
+  const int DA_USED = NSTRIP * NA_B + 2 * R;   // rows the strips read
 
-  // ---- Sobel^T: dU_c at the touched cells -------------------------------
-  for (int idx = tid; idx < NCI * NCJ; idx += NTHREADS) {
-    const int r = idx / NCJ, c = idx - (idx / NCJ) * NCJ;
-    int vi = ci_lo + r, vj = cj_lo + c;
-    float ux = 0.f, uy = 0.f;
-    bool real = true;
-    if (clamp) {
-      real = vi >= 0 && vi < g.nx && vj >= 0 && vj < g.ny;
-    } else {
-      vi = wrapi(vi, g.nx);
-      vj = wrapi(vj, g.ny);
+  // ---- stage u, the dA/dH seeds and the Sobel seeds ----------------------
+  for (int r = ty; r < DA_USED; r += 8) {
+    const int va = da_lo + r;
+    const bool row_ok = r < DA && (!clamp || (va >= 0 && va < g.mx));
+    const size_t rowo = row_ok ? (size_t)(clamp ? va : wrapi(va, g.mx)) * g.my : 0;
+    for (int c = tx; c < DB; c += 32) {
+      const int vb = db_lo + c;
+      const bool ok = row_ok && (!clamp || (vb >= 0 && vb < g.my));
+      const size_t o = ok ? rowo + (clamp ? vb : wrapi(vb, g.my)) : 0;
+      cp_async4(sU + r * DBP + c, a.pd4 + o, ok);
+      cp_async4(sIE2 + r * DBP + c, a.ie2 + o, ok);
     }
-    if (real) {
-      const SobelT tx = sobel_t_axis(vi, g.nx, g.bc);
-      const SobelT ty = sobel_t_axis(vj, g.ny, g.bc);
+  }
+  for (int r = ty; r < NCI; r += 8) {
+    const int vi = ci_lo + r;
+    const bool row_ok = !clamp || (vi >= 0 && vi < g.nx);
+    const size_t rowo = row_ok ? (size_t)(clamp ? vi : wrapi(vi, g.nx)) * g.ny : 0;
+    for (int c = tx; c < NCJ; c += 32) {
+      const int vj = cj_lo + c;
+      const bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
+      const size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
+      float *d = sSeed + r * S::NCJ + c;
+      cp_async4(d + 0 * S::NC, a.seeds + S_DAX * plane + o, ok);
+      cp_async4(d + 1 * S::NC, a.seeds + S_DHX * plane + o, ok);
+      cp_async4(d + 2 * S::NC, a.seeds + S_DAY * plane + o, ok);
+      cp_async4(d + 3 * S::NC, a.seeds + S_DHY * plane + o, ok);
+      cp_async4(d + 4 * S::NC, a.seeds + S_DAZ * plane + o, ok);
+      cp_async4(d + 5 * S::NC, a.seeds + S_DHZ * plane + o, ok);
+    }
+  }
+  for (int r = ty; r < NCI + 2; r += 8) {
+    const int vi = ci_lo - 1 + r;
+    const bool row_ok = !clamp || (vi >= 0 && vi < g.nx);
+    const size_t rowo = row_ok ? (size_t)(clamp ? vi : wrapi(vi, g.nx)) * g.ny : 0;
+    for (int c = tx; c < NCJ + 2; c += 32) {
+      const int vj = cj_lo - 1 + c;
+      const bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
+      const size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
+      float *d = sG + r * S::NGJ + c;
+      cp_async4(d + 0 * S::NG, a.seeds + S_GXX * plane + o, ok);
+      cp_async4(d + 1 * S::NG, a.seeds + S_GYX * plane + o, ok);
+      cp_async4(d + 2 * S::NG, a.seeds + S_GXY * plane + o, ok);
+      cp_async4(d + 3 * S::NG, a.seeds + S_GYY * plane + o, ok);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // ---- Sobel^T: dU_c at the touched cells ----------------------------------
+  // interior cells use the plain transposed stencil; cells next to an edge
+  // replicate use the folded weights
+  for (int c = tx; c < NCJ; c += 32) {
+    const int vj = cj_lo + c;
+    const bool col_real = vj >= 0 && vj < g.ny;
+    float wdy[3], wsy[3];
+    sobel_t_weights(clamp ? vj : wrapi(vj, g.ny), g.ny, BC, wdy, wsy);
+    for (int r = ty; r < NCI; r += 8) {
+      const int vi = ci_lo + r;
+      float ux = 0.f, uy = 0.f;
+      if (!clamp || (col_real && vi >= 0 && vi < g.nx)) {
+        float wdx[3], wsx[3];
+        sobel_t_weights(clamp ? vi : wrapi(vi, g.nx), g.nx, BC, wdx, wsx);
 #pragma unroll
-      for (int p = 0; p < 3; ++p) {
+        for (int e = 0; e < 3; ++e) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const size_t o = (size_t)tx.src[p] * g.ny + ty.src[q];
-          const float wdx_sy = tx.wd[p] * ty.ws[q];   // d g_x / d U
-          const float wsx_dy = tx.ws[p] * ty.wd[q];   // d g_y / d U
-          ux += wdx_sy * __ldg(a.seeds + S_GXX * plane + o) + wsx_dy * __ldg(a.seeds + S_GYX * plane + o);
-          uy += wdx_sy * __ldg(a.seeds + S_GXY * plane + o) + wsx_dy * __ldg(a.seeds + S_GYY * plane + o);
+          for (int f = 0; f < 3; ++f) {
+            const int o = (r + e) * S::NGJ + (c + f);   // source cell (vi - 1 + e, vj - 1 + f)
+            const float gx_w = wdx[e] * wsy[f];          // d g_x / d U
+            const float gy_w = wsx[e] * wdy[f];          // d g_y / d U
+            ux += gx_w * sG[0 * S::NG + o] + gy_w * sG[1 * S::NG + o];
+            uy += gx_w * sG[2 * S::NG + o] + gy_w * sG[3 * S::NG + o];
+          }
         }
       }
+      sdU[0 * S::NC + r * S::NCJ + c] = ux;
+      sdU[1 * S::NC + r * S::NCJ + c] = uy;
     }
-    sdUx[r * S::NCJ + c] = ux;
-    sdUy[r * S::NCJ + c] = uy;
   }
   __syncthreads();
 
-  // ---- du on the du region ---------------------------------------------
-  const int NSTRIP = (GA + NA_B - 1) / NA_B;
-  const int DA_USED = NSTRIP * NA_B + 2 * R;   // rows the strips read
+  // ---- du on the du region (in place over P' deps / 4) -----------------------
   const float q4 = 0.25f;
-  for (int idx = tid; idx < DA_USED * DB; idx += NTHREADS) {
-    const int r = idx / DB, c = idx - (idx / DB) * DB;
-    const int va = da_lo + r, vb = db_lo + c;
-    float du = 0.f;
-    const bool inside = va >= 0 && va < g.mx && vb >= 0 && vb < g.my;
-    if (r < DA && (inside || !clamp)) {
-      const int wa = clamp ? va : wrapi(va, g.mx);
-      const int wb = clamp ? vb : wrapi(vb, g.my);
-      const float u = __ldg(a.uws + (size_t)wa * g.my + wb);
-      const float t = tanhf(g.beta * (u - g.eta));
-      const float pprime = 0.5f * g.beta * (1.f - t * t);
-      const float e = fmaf(fmaf(0.5f, t, 0.5f), g.deps, g.eps_clad);
-      const float ie2 = 1.f / (e * e);
+  {
+    const FastDiv ddb((unsigned)DB);
+    for (int idx = tid; idx < DA * DB; idx += NTHREADS) {
+      const int r = (int)ddb.div((unsigned)idx), c = idx - r * DB;
+      const int va = da_lo + r, vb = db_lo + c;
+      if (clamp && (va < 0 || va >= g.mx || vb < 0 || vb >= g.my)) continue;   // stays zero
+      const float pd4 = sU[r * DBP + c];       // P'(u) (eps_core - eps_clad) / 4
+      const float ie2 = sIE2[r * DBP + c];     // 1 / eps^2
       // cells containing (va, vb): centred axis -> v >> 1, shifted axis -> (v+1) >> 1
-      const int ia_c = va >> 1, jb_c = vb >> 1;
-      const int ia_s = (va + 1) >> 1, jb_s = (vb + 1) >> 1;
+      const int ic = (va >> 1) - ci_lo, is = ((va + 1) >> 1) - ci_lo;
+      const int jc = (vb >> 1) - cj_lo, js = ((vb + 1) >> 1) - cj_lo;
       // multiplicities of the shifted axis (edge replicate maps subpixel -1 onto 0)
       float ma = 1.f, mb = 1.f;
       if (clamp) {
-        ma = ia_s >= g.nx ? 0.f : (va == 0 ? 2.f : 1.f);
-        mb = jb_s >= g.ny ? 0.f : (vb == 0 ? 2.f : 1.f);
+        ma = ((va + 1) >> 1) >= g.nx ? 0.f : (va == 0 ? 2.f : 1.f);
+        mb = ((vb + 1) >> 1) >= g.ny ? 0.f : (vb == 0 ? 2.f : 1.f);
       }
-      float de = 0.f, dus = 0.f;
-      // x: centred in a, shifted in b
-      if (mb != 0.f) {
-        const size_t o = (size_t)(clamp ? ia_c : wrapi(ia_c, g.nx)) * g.ny + (clamp ? jb_s : wrapi(jb_s, g.ny));
-        de += mb * (__ldg(a.seeds + S_DAX * plane + o) - __ldg(a.seeds + S_DHX * plane + o) * ie2);
-        dus += mb * sdUx[(ia_c - ci_lo) * S::NCJ + (jb_s - cj_lo)];
-      }
-      // y: shifted in a, centred in b
-      if (ma != 0.f) {
-        const size_t o = (size_t)(clamp ? ia_s : wrapi(ia_s, g.nx)) * g.ny + (clamp ? jb_c : wrapi(jb_c, g.ny));
-        de += ma * (__ldg(a.seeds + S_DAY * plane + o) - __ldg(a.seeds + S_DHY * plane + o) * ie2);
-        dus += ma * sdUy[(ia_s - ci_lo) * S::NCJ + (jb_c - cj_lo)];
-      }
-      // z: shifted in both
-      if (ma != 0.f && mb != 0.f) {
-        const size_t o = (size_t)(clamp ? ia_s : wrapi(ia_s, g.nx)) * g.ny + (clamp ? jb_s : wrapi(jb_s, g.ny));
-        de += ma * mb * (__ldg(a.seeds + S_DAZ * plane + o) - __ldg(a.seeds + S_DHZ * plane + o) * ie2);
-      }
-      du = q4 * fmaf(pprime * g.deps, de, dus);
+      const int ox = ic * S::NCJ + js;   // x: centred in a, shifted in b
+      const int oy = is * S::NCJ + jc;   // y: shifted in a, centred in b
+      const int oz = is * S::NCJ + js;   // z: shifted in both
+      const float de = mb * (sSeed[0 * S::NC + ox] - sSeed[1 * S::NC + ox] * ie2) +
+                       ma * (sSeed[2 * S::NC + oy] - sSeed[3 * S::NC + oy] * ie2) +
+                       ma * mb * (sSeed[4 * S::NC + oz] - sSeed[5 * S::NC + oz] * ie2);
+      const float dus = mb * sdU[0 * S::NC + ox] + ma * sdU[1 * S::NC + oy];
+      sU[r * DBP + c] = fmaf(pd4, de, q4 * dus);
     }
-    sdu[r * DBP + c] = du;
   }
   __syncthreads();
 
   // ---- K^T gather on the gather region ----------------------------------
-  for (int item = tid; item < NSTRIP * GB; item += NTHREADS) {
-    const int s = item / GB, col = item - (item / GB) * GB;
-    const int r0 = s * NA_B;
-    float hi[NA_B], lo[NA_B];
-    strip_stencil<RP1, NA_B, false>(sdu + r0 * DBP + col, DBP, a, hi, lo);
+  {
+    const FastDiv dgb((unsigned)GB);
+    for (int item = tid; item < NSTRIP * GB; item += NTHREADS) {
+      const int st = (int)dgb.div((unsigned)item), col = item - st * GB;
+      const int r0 = st * NA_B;
+      float hi[NA_B], lo[NA_B];
+      strip_stencil<RP1, NA_B, false>(sU + r0 * DBP + col, DBP, a, hi, lo);
 #pragma unroll
-    for (int k = 0; k < NA_B; ++k) {
-      if (r0 + k < GA) sdc[(r0 + k) * S::GB_MAX + col] = hi[k];
+      for (int k = 0; k < NA_B; ++k) {
+        if (r0 + k < GA) sdc[(r0 + k) * S::GB_MAX + col] = hi[k];
+      }
     }
   }
   __syncthreads();
 
   // ---- fold extended positions onto the edge and write ------------------
-  const int na = aend - a0, nb = bend - b0;
-  for (int idx = tid; idx < na * nb; idx += NTHREADS) {
-    const int r = idx / nb, c = idx - (idx / nb) * nb;
-    const int ga = a0 + r, gb = b0 + c;
-    int ra0 = ga - ga_lo, ra1 = ra0, rb0 = gb - gb_lo, rb1 = rb0;
+  for (int r = ty; r < aend - a0; r += 8) {
+    const int ga = a0 + r;
+    int ra0 = ga - ga_lo, ra1 = ra0;
     if (clamp) {
       if (ga == 0) ra0 = 0;
       if (ga == g.mx - 1) ra1 = GA - 1;
-      if (gb == 0) rb0 = 0;
-      if (gb == g.my - 1) rb1 = GB - 1;
     }
-    float acc = 0.f;
-    for (int x = ra0; x <= ra1; ++x)
-      for (int y = rb0; y <= rb1; ++y) acc += sdc[x * S::GB_MAX + y];
-    a.dJdC[(size_t)ga * g.my + gb] = acc;
+    for (int c = tx; c < bend - b0; c += 32) {
+      const int gb = b0 + c;
+      int rb0 = gb - gb_lo, rb1 = rb0;
+      if (clamp) {
+        if (gb == 0) rb0 = 0;
+        if (gb == g.my - 1) rb1 = GB - 1;
+      }
+      float acc = 0.f;
+      for (int x = ra0; x <= ra1; ++x)
+        for (int y = rb0; y <= rb1; ++y) acc += sdc[x * S::GB_MAX + y];
+      a.dJdC[(size_t)ga * g.my + gb] = acc;
+    }
   }
 }
 

@@ -25,8 +25,8 @@ static_assert(UA % NA_F == 0, "forward strips must tile the subpixel rows");
 
 // backward tile (subpixels)
 constexpr int TA = 32;
-constexpr int TB = 64;
-constexpr int NA_B = 8;
+constexpr int TB = 32;
+constexpr int NA_B = 4;
 
 // filter radius limit: RP1 = ceil(R) taps per half-axis including the centre
 constexpr int MAX_RP1 = 12;
@@ -36,6 +36,10 @@ constexpr int MAX_BOX = 2 * MAX_RP1 - 1;
 constexpr float NORMAL_TAU2 = 1e-12f;
 
 enum Mode : int { MODE_FWD = 0, MODE_C64 = 1, MODE_REAL = 2 };
+
+// bits of the device-side error flag
+constexpr int ERRFLAG_TIMEOUT = 1;   // a bounded wait gave up
+constexpr int ERRFLAG_BOUNDS = 2;    // a bounds check fired
 
 // seed planes written by the forward/contraction kernel, [NSEED][nx][ny]
 enum Seed : int {
@@ -55,24 +59,23 @@ struct FwdArgs {
   int mode;
   int write_eps;
   int write_offdiag;
-  int nlambda;
+  int stage_floats;              // shared floats available for eps_hat staging
   const float *C;
   float *eps;
   float *offdiag;
-  const float *G;
+  const float *W;                // [4][nx][ny] Eq. 1 column sums (contraction kernel)
   float *seeds;
-  float *uws;
+  float *pd4;                    // [mx][my] P'(u) (eps_core - eps_clad) / 4
+  float *ie2;                    // [mx][my] 1 / eps^2
   int *err;
-  const float4 *EF[EPS_MAX_LAMBDA];
-  const float4 *EA[EPS_MAX_LAMBDA];
-  float fs[EPS_MAX_LAMBDA][3];   // scale * s_F * s_A per wavelength and component
   float w[MAX_BOX * MAX_BOX];    // conic weights, dense (2 RP1 - 1)^2 box, row-major
 };
 
 struct BwdArgs {
   Geometry g;
   const float *seeds;
-  const float *uws;
+  const float *pd4;
+  const float *ie2;
   float *dJdC;
   int *err;
   float w[MAX_BOX * MAX_BOX];
@@ -87,6 +90,50 @@ __device__ __forceinline__ int wrapi(int x, int n) {
 
 __device__ __forceinline__ int bc_map(int x, int n, int bc) {
   return bc == EPS_BC_CLAMP ? clampi(x, 0, n - 1) : wrapi(x, n);
+}
+
+// Asynchronous 4-byte global -> shared copy (cp.async); zero-fills the
+// destination when `valid` is false (no bytes are read from `src` then).
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src), "r"(n)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Bulk (TMA) copy of `bytes` contiguous bytes from shared to global memory,
+// tracked by the calling thread's bulk async-group.  Both addresses 16-byte
+// aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, unsigned bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(s),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// shared memory read by earlier bulk stores of this thread may be reused
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// earlier bulk stores of this thread have completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// make this thread's generic-proxy shared-memory writes visible to bulk copies
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// Programmatic dependent launch: wait until the grids this grid depends on
+// have completed and their writes are visible (no-op without a dependency).
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+// Let the dependent grid in the stream start launching its blocks.
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
 // Knuth's TwoSum: hi + lo += x with the rounding error of the add kept in lo.

@@ -2,17 +2,19 @@
 // columns per block.
 //
 // Stages (all in shared memory except the field reads and the outputs):
-//   1. C tile with a halo of R + 3 subpixels, boundary rule applied on load.
+//   1. C tile with a halo of R + 3 subpixels (asynchronous copies), boundary
+//      rule applied on load.
 //   2. u = K * C (Eq. 2) on the (2 TI + 5) x (2 TJ + 5) subpixel region the
 //      dual cells and the Sobel halo touch, then rho (Eq. 6), eps = mix(rho)
 //      and 1/eps.
 //   3. Dual-cell means (Eq. 8): A_c, H_c for the tile's cells, U_x, U_y for
 //      the tile plus a one-cell halo; Sobel gradients and normal weights.
-//   4. Eq. 7 per column; eps_hat written for every z plane.
-//   5. (VJP) W = sum over the slab planes of scale * Re(E_F E_A) (Eq. 1), or
-//      of a real cotangent G; only the J-support planes are read.
-//   6. (VJP) per-column seeds dJ/dA_c, dJ/dH_c, dJ/dg and the tile's u are
-//      written to the workspace for the scatter kernel.
+//   4. Eq. 7 per column; eps_hat rows written with warp-contiguous 16-byte
+//      streaming stores.
+//   5. (VJP) the column sums W of Eq. 1 (contraction kernel) are read, and
+//   6. per-column seeds dJ/dA_c, dJ/dH_c, dJ/dg are written to the
+//      workspace; stage 2 already wrote the per-subpixel adjoint factors
+//      P'(u) (eps_core - eps_clad) / 4 and 1/eps^2 of the tile.
 #pragma once
 
 #include "epsc_common.cuh"
@@ -32,43 +34,41 @@ struct FwdSmem {
   static constexpr int OFF_IE = OFF_E + UA * UB;
   static constexpr int OFF_UX = OFF_IE + UA * UB;
   static constexpr int OFF_UY = OFF_UX + HN;
-  static constexpr int OFF_W = OFF_UY + HN;      // 4 x NTHREADS contraction sums
-  static constexpr int OFF_EPS = OFF_W + 4 * NTHREADS;   // 6 x NTHREADS column values
-  static constexpr int TOTAL = OFF_EPS + 6 * NTHREADS;
+  static constexpr int TOTAL = OFF_UY + HN;
   static constexpr size_t BYTES = sizeof(float) * TOTAL;
+  // dynamic shared memory of a launch: max(BYTES, the eps_hat staging area)
 };
 
-__device__ __forceinline__ float4 ld_stream(const float4 *p) {
-  float4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(p));
-  return v;
-}
-
-// value of eps_hat component `comp` on plane k given the column's Eq. 7 values
-__device__ __forceinline__ float plane_value(int comp, int k, int k0, int nk, float exy, float ezi,
-                                             float ezf, float clad) {
-  if (comp < 2) return (k >= k0 + 1 && k <= k0 + nk) ? exy : clad;
-  if (k >= k0 + 1 && k <= k0 + nk - 1) return ezi;
-  if (k == k0 || k == k0 + nk) return ezf;
+// Value of output component `comp` on plane k: comp 0/1 = eps_xx/yy and
+// 3/4 = off-diagonal at the Ex/Ey points take `vmain` on the slab planes;
+// comp 2 = eps_zz takes vzi inside the slab and vzf on the two face planes.
+__device__ __forceinline__ float plane_value(int comp, int k, int k0, int nk, float vmain,
+                                             float vzi, float vzf, float clad) {
+  const bool slab = k >= k0 + 1 && k <= k0 + nk;
+  if (comp < 2) return slab ? vmain : clad;
+  if (comp > 2) return slab ? vmain : 0.f;
+  if (k >= k0 + 1 && k <= k0 + nk - 1) return vzi;
+  if (k == k0 || k == k0 + nk) return vzf;
   return clad;
 }
 
-template <int RP1>
-__global__ void __launch_bounds__(NTHREADS) fwd_kernel(const __grid_constant__ FwdArgs a) {
+template <int BC>
+__device__ __forceinline__ int bc_map_t(int x, int n) {
+  return BC == EPS_BC_CLAMP ? clampi(x, 0, n - 1) : wrapi(x, n);
+}
+
+template <int RP1, int BC>
+__global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant__ FwdArgs a) {
   using S = FwdSmem<RP1>;
   constexpr int R = S::R;
   constexpr int CB = S::CB;
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   float *sC = smem + S::OFF_C;
   float *su = smem + S::OFF_U;
   float *se = smem + S::OFF_E;
   float *sie = smem + S::OFF_IE;
   float *sUx = smem + S::OFF_UX;
   float *sUy = smem + S::OFF_UY;
-  float *sW = smem + S::OFF_W;
-  float *sE = smem + S::OFF_EPS;
 
   const Geometry &g = a.g;
   const int tid = threadIdx.x;
@@ -78,40 +78,58 @@ __global__ void __launch_bounds__(NTHREADS) fwd_kernel(const __grid_constant__ F
   const int ub0 = 2 * j0 - 3;
   const int ca0 = ua0 - R;
   const int cb0 = ub0 - R;
+  const int nvi = min(TI, g.nx - i0);
+  const int nvj = min(TJ, g.ny - j0);
 
-  // ---- 1. control tile with halo --------------------------------------
+  // ---- 1. control tile with halo (asynchronous copies) ----------------
   for (int idx = tid; idx < S::CA * CB; idx += NTHREADS) {
     const int r = idx / CB;
     const int c = idx - r * CB;
-    const int ga = bc_map(ca0 + r, g.mx, g.bc);
-    const int gb = bc_map(cb0 + c, g.my, g.bc);
-    sC[idx] = __ldg(a.C + (size_t)ga * g.my + gb);
+    const int ga = bc_map_t<BC>(ca0 + r, g.mx);
+    const int gb = bc_map_t<BC>(cb0 + c, g.my);
+    cp_async4(sC + idx, a.C + (size_t)ga * g.my + gb, true);
   }
+  cp_async_wait_all();
   __syncthreads();
 
   // ---- 2. filtered density, projection, mixing -------------------------
+  // rho = (1 + tanh(x)) / 2 = 1 / (1 + exp(-2x)), x = beta (u - eta); the
+  // adjoint factor P'(u) (eps_core - eps_clad) / 4 = beta/2 deps rho (1 - rho)
+  // with 1 - rho = exp(-2x) rho, and 1/eps^2 of the core subpixels go to the
+  // workspace for the scatter kernel.
   constexpr int NSTRIP = UA / NA_F;
+  const bool vjp = a.mode != MODE_FWD;
   for (int item = tid; item < NSTRIP * UB; item += NTHREADS) {
     const int s = item / UB;
     const int col = item - s * UB;
     const int r0 = s * NA_F;
     float hi[NA_F], lo[NA_F];
-    strip_stencil<RP1, NA_F, true>(sC + r0 * CB + col, CB, a, hi, lo);
+    strip_stencil<RP1, NA_F, false>(sC + r0 * CB + col, CB, a, hi, lo);
 #pragma unroll
     for (int k = 0; k < NA_F; ++k) {
       const int o = (r0 + k) * UB + col;
-      const float x = g.beta * ((hi[k] - g.eta) + lo[k]);
-      const float rho = fmaf(0.5f, tanhf(x), 0.5f);
+      const float x = g.beta * (hi[k] - g.eta);
+      const float ex2 = __expf(-2.f * x);
+      const float rho = __fdividef(1.f, 1.f + ex2);
       const float e = fmaf(rho, g.deps, g.eps_clad);
-      su[o] = hi[k] + lo[k];
+      const float ie = __frcp_rn(e);
+      su[o] = hi[k];
       se[o] = e;
-      sie[o] = 1.0f / e;
+      sie[o] = ie;
+      if (vjp) {
+        const int ra = r0 + k - 3, rb = col - 3;   // core subpixel of the tile?
+        if (ra >= 0 && ra < 2 * nvi && rb >= 0 && rb < 2 * nvj) {
+          const size_t go = (size_t)(2 * i0 + ra) * g.my + 2 * j0 + rb;
+          a.pd4[go] = 0.5f * g.beta * g.deps * (ex2 * rho * rho);
+          a.ie2[go] = ie * ie;
+        }
+      }
     }
   }
   __syncthreads();
 
   // edge replicate: subpixels outside the region take the edge subpixel's values
-  if (g.bc == EPS_BC_CLAMP && (ua0 < 0 || ub0 < 0 || ua0 + UA > g.mx || ub0 + UB > g.my)) {
+  if (BC == EPS_BC_CLAMP && (ua0 < 0 || ub0 < 0 || ua0 + UA > g.mx || ub0 + UB > g.my)) {
     for (int idx = tid; idx < UA * UB; idx += NTHREADS) {
       const int r = idx / UB;
       const int c = idx - r * UB;
@@ -133,7 +151,7 @@ __global__ void __launch_bounds__(NTHREADS) fwd_kernel(const __grid_constant__ F
     const int hr = idx / S::HP;
     const int hc = idx - hr * S::HP;
     int ci = i0 - 1 + hr, cj = j0 - 1 + hc;
-    if (g.bc == EPS_BC_CLAMP) {
+    if (BC == EPS_BC_CLAMP) {
       ci = clampi(ci, 0, g.nx - 1);
       cj = clampi(cj, 0, g.ny - 1);
     }
@@ -179,185 +197,125 @@ __global__ void __launch_bounds__(NTHREADS) fwd_kernel(const __grid_constant__ F
   const float g2x = gxx * gxx + gyx * gyx;
   const float g2y = gxy * gxy + gyy * gyy;
   const bool okx = g2x > NORMAL_TAU2, oky = g2y > NORMAL_TAU2;
-  const float mx_ = okx ? gxx * gxx / g2x : 0.f;
-  const float my_ = oky ? gyy * gyy / g2y : 0.f;
+  const float ig2x = okx ? __frcp_rn(g2x) : 0.f;
+  const float ig2y = oky ? __frcp_rn(g2y) : 0.f;
+  const float mx_ = gxx * gxx * ig2x;
+  const float my_ = gyy * gyy * ig2y;
 
   // ---- 4. Eq. 7 and the eps_hat store ----------------------------------
-  const float ex = 1.0f / fmaf(mx_, Hx, (1.f - mx_) / Ax);
-  const float ey = 1.0f / fmaf(my_, Hy, (1.f - my_) / Ay);
-  const float ezi = Az;
-  const float ezf = 1.0f / fmaf(0.5f, Hz, 0.5f / g.eps_clad);
-  sE[0 * NTHREADS + tid] = ex;
-  sE[1 * NTHREADS + tid] = ey;
-  sE[2 * NTHREADS + tid] = ezi;
-  sE[3 * NTHREADS + tid] = ezf;
-  if (a.write_offdiag) {
-    sE[4 * NTHREADS + tid] = okx ? gxx * gyx / g2x * (Hx - 1.f / Ax) : 0.f;
-    sE[5 * NTHREADS + tid] = oky ? gxy * gyy / g2y * (Hy - 1.f / Ay) : 0.f;
-  }
-  __syncthreads();
+  const float iAx = __frcp_rn(Ax), iAy = __frcp_rn(Ay);
+  const float ex = __frcp_rn(fmaf(mx_, Hx, (1.f - mx_) * iAx));
+  const float ey = __frcp_rn(fmaf(my_, Hy, (1.f - my_) * iAy));
+  const float ezf = __frcp_rn(fmaf(0.5f, Hz, 0.5f / g.eps_clad));
+  const float ezi = Az;   // n_z = 0 inside the slab: eps_zz = <eps>_z
+  const float odx = gxx * gyx * ig2x * (Hx - iAx);
+  const float ody = gxy * gyy * ig2y * (Hy - iAy);
 
-  const int nvi = min(TI, g.nx - i0);
-  const int nvj = min(TJ, g.ny - j0);
+  // ---- eps_hat store: whole-tile staging + bulk (TMA) stores ------------
+  // Each thread writes its column's planes of `ncomp` components into shared
+  // memory (rows of TJ * nz floats per component and tile row), then one
+  // thread issues one bulk copy per contiguous row span.  The copies run
+  // while the block goes on to the seeds; the block waits for them only
+  // before it exits.  When the staging does not fit, components go in
+  // rounds (waiting for the previous round's copies to read shared memory),
+  // and plane counts that are not a multiple of 4 use direct stores.
+  bool bulk_pending = false;
   if (a.write_eps || a.write_offdiag) {
-    const int ncomp_eps = a.write_eps ? 3 : 0;
-    const int ncomp = ncomp_eps + (a.write_offdiag ? 2 : 0);
-    if ((g.nz & 3) == 0) {
+    const int c_first = a.write_eps ? 0 : 3;
+    const int c_last = a.write_offdiag ? 4 : 2;
+    const size_t cplane = (size_t)g.nx * g.ny * g.nz;
+    const int comp_floats = TI * TJ * g.nz;
+    const int per_round = a.stage_floats / comp_floats;
+    if ((g.nz & 3) == 0 && per_round >= 1) {
+      float *sbuf = smem;   // the stencil buffers are dead from here on
       const int nz4 = g.nz >> 2;
-      const FastDiv dz4(nz4);
-      const int per_row = nvj * nz4;
-      for (int t = 0; t < ncomp; ++t) {
-        const bool od = t >= ncomp_eps;
-        const int comp = od ? t - ncomp_eps : t;
-        float *base = od ? a.offdiag : a.eps;
-        for (int r = 0; r < nvi; ++r) {
-          float4 *dst = reinterpret_cast<float4 *>(
-              base + (((size_t)comp * g.nx + i0 + r) * g.ny + j0) * g.nz);
-          for (int f = tid; f < per_row; f += NTHREADS) {
-            const int c = dz4.div(f);
-            const int k = 4 * (f - c * nz4);
-            const int col = r * TJ + c;
-            float4 v;
-            if (od) {
-              const float val = sE[(4 + comp) * NTHREADS + col];
-              v.x = (k + 0 >= g.k0 + 1 && k + 0 <= g.k0 + g.nk) ? val : 0.f;
-              v.y = (k + 1 >= g.k0 + 1 && k + 1 <= g.k0 + g.nk) ? val : 0.f;
-              v.z = (k + 2 >= g.k0 + 1 && k + 2 <= g.k0 + g.nk) ? val : 0.f;
-              v.w = (k + 3 >= g.k0 + 1 && k + 3 <= g.k0 + g.nk) ? val : 0.f;
-            } else {
-              const float exy = sE[comp * NTHREADS + col];
-              const float vzi = sE[2 * NTHREADS + col], vzf = sE[3 * NTHREADS + col];
-              v.x = plane_value(comp, k + 0, g.k0, g.nk, exy, vzi, vzf, g.eps_clad);
-              v.y = plane_value(comp, k + 1, g.k0, g.nk, exy, vzi, vzf, g.eps_clad);
-              v.z = plane_value(comp, k + 2, g.k0, g.nk, exy, vzi, vzf, g.eps_clad);
-              v.w = plane_value(comp, k + 3, g.k0, g.nk, exy, vzi, vzf, g.eps_clad);
-            }
-            __stcs(dst + f, v);
-          }
+      __syncthreads();
+      for (int c0 = c_first; c0 <= c_last; c0 += per_round) {
+        const int c1 = min(c_last, c0 + per_round - 1);
+        if (c0 != c_first) {   // previous round's copies must have read the buffer
+          if (tid == 0) bulk_wait_read();
+          __syncthreads();
         }
-      }
-    } else {
-      const FastDiv dz(g.nz);
-      const int per_row = nvj * g.nz;
-      for (int t = 0; t < ncomp; ++t) {
-        const bool od = t >= ncomp_eps;
-        const int comp = od ? t - ncomp_eps : t;
-        float *base = od ? a.offdiag : a.eps;
-        for (int r = 0; r < nvi; ++r) {
-          float *dst = base + (((size_t)comp * g.nx + i0 + r) * g.ny + j0) * g.nz;
-          for (int f = tid; f < per_row; f += NTHREADS) {
-            const int c = dz.div(f);
-            const int k = f - c * g.nz;
-            const int col = r * TJ + c;
-            float v;
-            if (od) {
-              v = (k >= g.k0 + 1 && k <= g.k0 + g.nk) ? sE[(4 + comp) * NTHREADS + col] : 0.f;
-            } else {
-              v = plane_value(comp, k, g.k0, g.nk, sE[comp * NTHREADS + col],
-                              sE[2 * NTHREADS + col], sE[3 * NTHREADS + col], g.eps_clad);
-            }
-            __stcs(dst + f, v);
-          }
-        }
-      }
-    }
-  }
-  if (a.mode == MODE_FWD) return;
-
-  // ---- 5. Eq. 1 contraction over the J-support planes ------------------
-  {
-    const int warp = tid >> 5, lane = tid & 31;
-    const int grp = lane >> 3, gl = lane & 7;
-    const int klo = g.k0, khi = g.k0 + g.nk;
-    for (int pass = 0; pass < NTHREADS / 32; ++pass) {
-      const int slot = pass * 32 + warp * 4 + grp;
-      const int r = slot / TJ, c = slot - (slot / TJ) * TJ;
-      const int pi = i0 + r, pj = j0 + c;
-      float wx = 0.f, wy = 0.f, wzi = 0.f, wzf = 0.f;
-      if (pi < g.nx && pj < g.ny) {
-        if (a.mode == MODE_C64) {
-          const int nz2 = g.nz >> 1;
-          const size_t cs = (size_t)g.nx * g.ny * nz2;       // component stride, float4
-          const size_t col = ((size_t)pi * g.ny + pj) * nz2;
-          const int plo = klo >> 1, phi = khi >> 1;
-          for (int l = 0; l < a.nlambda; ++l) {
-            const float4 *ef = a.EF[l] + col;
-            const float4 *ea = a.EA[l] + col;
-            for (int pc = plo + gl; pc <= phi; pc += 8) {
-              const float4 fx = ld_stream(ef + pc), ax = ld_stream(ea + pc);
-              const float4 fy = ld_stream(ef + cs + pc), ay = ld_stream(ea + cs + pc);
-              const float4 fz = ld_stream(ef + 2 * cs + pc), az = ld_stream(ea + 2 * cs + pc);
-              const int k = 2 * pc;
-              const bool s0 = k >= klo + 1 && k <= khi;
-              const bool s1 = k + 1 >= klo + 1 && k + 1 <= khi;
-              const bool i0z = k >= klo + 1 && k <= khi - 1;
-              const bool i1z = k + 1 >= klo + 1 && k + 1 <= khi - 1;
-              const bool f0z = k == klo || k == khi;
-              const bool f1z = k + 1 == klo || k + 1 == khi;
-              const float x0 = fx.x * ax.x - fx.y * ax.y, x1 = fx.z * ax.z - fx.w * ax.w;
-              const float y0 = fy.x * ay.x - fy.y * ay.y, y1 = fy.z * ay.z - fy.w * ay.w;
-              const float z0 = fz.x * az.x - fz.y * az.y, z1 = fz.z * az.z - fz.w * az.w;
-              wx = fmaf(a.fs[l][0], (s0 ? x0 : 0.f) + (s1 ? x1 : 0.f), wx);
-              wy = fmaf(a.fs[l][1], (s0 ? y0 : 0.f) + (s1 ? y1 : 0.f), wy);
-              wzi = fmaf(a.fs[l][2], (i0z ? z0 : 0.f) + (i1z ? z1 : 0.f), wzi);
-              wzf = fmaf(a.fs[l][2], (f0z ? z0 : 0.f) + (f1z ? z1 : 0.f), wzf);
-            }
-          }
-        } else {   // MODE_REAL: G is the cotangent of eps_hat itself
-          const size_t cs = (size_t)g.nx * g.ny * g.nz;
-          const float *gc = a.G + ((size_t)pi * g.ny + pj) * g.nz;
-          for (int k = klo + gl; k <= khi; k += 8) {
-            const float gx_ = __ldg(gc + k), gy_ = __ldg(gc + cs + k), gz_ = __ldg(gc + 2 * cs + k);
-            if (k >= klo + 1) {
-              wx += gx_;
-              wy += gy_;
-            }
-            if (k >= klo + 1 && k <= khi - 1) wzi += gz_;
-            if (k == klo || k == khi) wzf += gz_;
-          }
-        }
-      }
+        if (cr < nvi && cc < nvj) {
+          for (int comp = c0; comp <= c1; ++comp) {
+            const float vin = comp == 0 ? ex : comp == 1 ? ey : comp == 2 ? ezi : comp == 3 ? odx : ody;
+            const float out = comp < 3 ? g.eps_clad : 0.f;
+            const int zlen = comp == 2 ? g.nk - 1 : g.nk;   // planes k0+1 .. k0+zlen take vin
+            const int kf0 = comp == 2 ? g.k0 : -8, kf1 = comp == 2 ? g.k0 + g.nk : -8;
+            float4 *dst = reinterpret_cast<float4 *>(sbuf + (comp - c0) * comp_floats +
+                                                     (cr * TJ + cc) * g.nz);
+            for (int k4 = 0; k4 < nz4; ++k4) {
+              float t[4];
 #pragma unroll
-      for (int off = 4; off > 0; off >>= 1) {
-        wx += __shfl_xor_sync(0xffffffffu, wx, off);
-        wy += __shfl_xor_sync(0xffffffffu, wy, off);
-        wzi += __shfl_xor_sync(0xffffffffu, wzi, off);
-        wzf += __shfl_xor_sync(0xffffffffu, wzf, off);
+              for (int q = 0; q < 4; ++q) {
+                const int k = 4 * k4 + q;
+                const bool in = (unsigned)(k - (g.k0 + 1)) < (unsigned)zlen;
+                const bool face = k == kf0 || k == kf1;
+                t[q] = in ? vin : (face ? ezf : out);
+              }
+              dst[k4] = make_float4(t[0], t[1], t[2], t[3]);
+            }
+          }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          for (int comp = c0; comp <= c1; ++comp) {
+            float *base = comp < 3 ? a.eps + comp * cplane : a.offdiag + (comp - 3) * cplane;
+            for (int r = 0; r < nvi; ++r)
+              bulk_store(base + ((size_t)(i0 + r) * g.ny + j0) * g.nz,
+                         sbuf + (comp - c0) * comp_floats + r * TJ * g.nz,
+                         (unsigned)(nvj * g.nz * 4));
+          }
+          bulk_commit();
+        }
+        bulk_pending = true;
       }
-      if (gl == 0) {
-        sW[0 * NTHREADS + slot] = wx;
-        sW[1 * NTHREADS + slot] = wy;
-        sW[2 * NTHREADS + slot] = wzi;
-        sW[3 * NTHREADS + slot] = wzf;
+    } else if (valid) {
+      // plane counts not a multiple of 4: thread per column
+      for (int comp = c_first; comp <= c_last; ++comp) {
+        float *base = comp < 3 ? a.eps + comp * cplane : a.offdiag + (comp - 3) * cplane;
+        const float vm = comp == 0 ? ex : comp == 1 ? ey : comp == 3 ? odx : ody;
+        float *dst = base + ((size_t)ci * g.ny + cj) * g.nz;
+        for (int k = 0; k < g.nz; ++k)
+          dst[k] = plane_value(comp, k, g.k0, g.nk, vm, ezi, ezf, g.eps_clad);
       }
     }
   }
-  __syncthreads();
+  if (a.mode == MODE_FWD) {
+    if (bulk_pending && tid == 0) bulk_wait_all();
+    return;
+  }
 
-  // ---- 6. adjoint seeds and the tile's u -------------------------------
+  // ---- 5. Eq. 1 contraction sums of this tile's columns ------------------
+  // (computed by the contraction kernel; read them once the grid that wrote
+  // them has completed)
+  griddep_wait();
+  // ---- 6. adjoint seeds -------------------------------------------------
   if (valid) {
-    const float Wx = sW[0 * NTHREADS + tid], Wy = sW[1 * NTHREADS + tid];
-    const float Wzi = sW[2 * NTHREADS + tid], Wzf = sW[3 * NTHREADS + tid];
+    const size_t plane = (size_t)g.nx * g.ny;
+    const float *wc = a.W + (size_t)ci * g.ny + cj;
+    const float Wx = wc[0 * plane], Wy = wc[1 * plane];
+    const float Wzi = wc[2 * plane], Wzf = wc[3 * plane];
     // eps = 1/(m H + (1-m)/A):  de/dH = -eps^2 m, de/dA = eps^2 (1-m)/A^2, de/dm = -eps^2 (H - 1/A)
     const float e2x = ex * ex * Wx, e2y = ey * ey * Wy;
-    const float dAx = e2x * (1.f - mx_) / (Ax * Ax), dHx = -e2x * mx_;
-    const float dmx = -e2x * (Hx - 1.f / Ax);
-    const float dAy = e2y * (1.f - my_) / (Ay * Ay), dHy = -e2y * my_;
-    const float dmy = -e2y * (Hy - 1.f / Ay);
+    const float dAx = e2x * (1.f - mx_) * (iAx * iAx), dHx = -e2x * mx_;
+    const float dmx = -e2x * (Hx - iAx);
+    const float dAy = e2y * (1.f - my_) * (iAy * iAy), dHy = -e2y * my_;
+    const float dmy = -e2y * (Hy - iAy);
     float dgxx = 0.f, dgyx = 0.f, dgxy = 0.f, dgyy = 0.f;
     if (okx) {   // m = gx^2/|g|^2: dm/dgx = 2 gx gy^2/|g|^4, dm/dgy = -2 gx^2 gy/|g|^4
-      const float t = 2.f * dmx / (g2x * g2x);
+      const float t = 2.f * dmx * (ig2x * ig2x);
       dgxx = t * gxx * gyx * gyx;
       dgyx = -t * gxx * gxx * gyx;
     }
     if (oky) {   // m = gy^2/|g|^2: dm/dgx = -2 gx gy^2/|g|^4, dm/dgy = 2 gx^2 gy/|g|^4
-      const float t = 2.f * dmy / (g2y * g2y);
+      const float t = 2.f * dmy * (ig2y * ig2y);
       dgxy = -t * gxy * gyy * gyy;
       dgyy = t * gxy * gxy * gyy;
     }
     const float dAz = Wzi;
     const float dHz = -0.5f * ezf * ezf * Wzf;
-    const size_t plane = (size_t)g.nx * g.ny;
     float *sd = a.seeds + (size_t)ci * g.ny + cj;
     sd[S_DAX * plane] = dAx;
     sd[S_DHX * plane] = dHx;
@@ -370,15 +328,7 @@ __global__ void __launch_bounds__(NTHREADS) fwd_kernel(const __grid_constant__ F
     sd[S_DAZ * plane] = dAz;
     sd[S_DHZ * plane] = dHz;
   }
-  {
-    const int na = 2 * nvi, nb = 2 * nvj;
-    for (int idx = tid; idx < 4 * TI * TJ; idx += NTHREADS) {
-      const int r = idx / (2 * TJ);
-      const int c = idx - r * (2 * TJ);
-      if (r < na && c < nb)
-        a.uws[(size_t)(2 * i0 + r) * g.my + 2 * j0 + c] = su[(r + 3) * UB + c + 3];
-    }
-  }
+  if (bulk_pending && tid == 0) bulk_wait_all();
 }
 
 }  // namespace epsc

@@ -14,12 +14,21 @@ struct KernelEntry {
 
 // Defined in the instantiation units (RP1 1..6 in *_a, 7..12 in *_b);
 // return {nullptr, 0} outside their range.
-KernelEntry fwd_entry_a(int rp1);
-KernelEntry fwd_entry_b(int rp1);
-KernelEntry bwd_entry_a(int rp1);
-KernelEntry bwd_entry_b(int rp1);
+KernelEntry fwd_entry_a(int rp1, int bc);
+KernelEntry fwd_entry_b(int rp1, int bc);
+KernelEntry bwd_entry_a(int rp1, int bc);
+KernelEntry bwd_entry_b(int rp1, int bc);
 
-inline KernelEntry fwd_entry(int rp1) { return rp1 <= 6 ? fwd_entry_a(rp1) : fwd_entry_b(rp1); }
-inline KernelEntry bwd_entry(int rp1) { return rp1 <= 6 ? bwd_entry_a(rp1) : bwd_entry_b(rp1); }
+// Contraction kernel with 4 or 8 lanes per column.
+const void *contract_entry(int lanes);
+// Contraction kernel fed by bulk tensor copies (complex64 fields).
+const void *contract_tma_entry();
+
+inline KernelEntry fwd_entry(int rp1, int bc) {
+  return rp1 <= 6 ? fwd_entry_a(rp1, bc) : fwd_entry_b(rp1, bc);
+}
+inline KernelEntry bwd_entry(int rp1, int bc) {
+  return rp1 <= 6 ? bwd_entry_a(rp1, bc) : bwd_entry_b(rp1, bc);
+}
 
 }  // namespace epsc

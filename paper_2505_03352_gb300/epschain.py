@@ -99,6 +99,7 @@ _PROTOS = {
                                     ctypes.c_size_t, _VP]),
     "eps_sync_status": (ctypes.c_int, [_VP]),
     "eps_profile_start": (ctypes.c_int, []),
+    "eps_set_l2_fetch_granularity": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "eps_profile_stop": (ctypes.c_int, [ctypes.POINTER(eps_profile_entry_t), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]),
 }
@@ -257,6 +258,15 @@ def eps_vjp_real(prob: Problem, C, G, dJdC=None, ws=None, stream=None):
 
 def eps_sync_status(stream=None):
     _check(lib().eps_sync_status(_stream(stream)), "eps_sync_status")
+
+
+def eps_set_l2_fetch_granularity(nbytes: int) -> int:
+    """Set the current context's L2 fetch granularity hint; returns the
+    previous value."""
+    prev = ctypes.c_int32(0)
+    _check(lib().eps_set_l2_fetch_granularity(int(nbytes), ctypes.byref(prev)),
+           "eps_set_l2_fetch_granularity")
+    return prev.value
 
 
 def eps_profile_start():

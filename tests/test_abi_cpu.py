@@ -66,10 +66,11 @@ def prob(**kw):
 def test_workspace_size_layout(L):
     p = prob(mx=600, my=600, nz=24)
     n = ec.eps_workspace_size(p)
-    seeds = 10 * 300 * 300 * 4
-    u = 600 * 600 * 4
+    w = 4 * 300 * 300 * 4          # Eq. 1 column sums
+    seeds = 10 * 300 * 300 * 4     # adjoint seeds per Yee column
+    sub = 600 * 600 * 4            # per-subpixel adjoint factors (two maps)
     al = lambda b: (b + 255) // 256 * 256
-    assert n == al(seeds) + al(u)
+    assert n == al(w) + al(seeds) + 2 * al(sub)
     assert ec.eps_workspace_size(prob(mx=0)) == 0
 
 

@@ -217,3 +217,46 @@ def test_empty_region_is_a_no_op():
     e = ec.eps_forward(p, C)
     assert e.numel() == 0
     ec.eps_sync_status()
+
+
+def test_values_outside_the_support_planes_are_never_read_into_the_sum():
+    # NaN in every cladding plane of the fields: the gradient must be finite
+    # and equal to the one with those planes zeroed.
+    ec = _ec()
+    p, o = problems(64, 96, 24, 3.0, 8.0)
+    rng = np.random.default_rng(9)
+    C = rng.random((64, 96), dtype=np.float32)
+    shape = (3, p.nx, p.ny, 24)
+    EF = synth.complex_field(shape, 31)
+    EA = synth.complex_field(shape, 32)
+    k0, nk = p.k0, 11
+    mask = np.ones(shape, bool)
+    mask[0:2, :, :, k0 + 1:k0 + nk + 1] = False
+    mask[2, :, :, k0:k0 + nk + 1] = False
+    EFn, EAn = EF.copy(), EA.copy()
+    EFn[mask] = np.nan
+    EAn[mask] = np.nan
+    g_nan, _ = run_vjp(p, C, [EFn], [EAn], eps_out=False)
+    EFz, EAz = EF.copy(), EA.copy()
+    EFz[mask] = 0
+    EAz[mask] = 0
+    g_zero, _ = run_vjp(p, C, [EFz], [EAz], eps_out=False)
+    assert np.all(np.isfinite(g_nan))
+    np.testing.assert_array_equal(g_nan, g_zero)
+    assert grad_err(g_nan, orc.vjp_fields(o, C, [EFz], [EAz])) <= GRAD_TOL
+
+
+def test_l2_fetch_granularity_does_not_change_results():
+    ec = _ec()
+    w = synth.WORKLOADS[1]
+    p, o = problems(w.mx, w.my, w.nz, w.radius, w.beta)
+    C = synth.controls(w)
+    EF, EA = synth.fields(w)
+    prev = ec.eps_set_l2_fetch_granularity(32)
+    try:
+        g32, e32 = run_vjp(p, C, EF, EA)
+    finally:
+        ec.eps_set_l2_fetch_granularity(prev)
+    g, e = run_vjp(p, C, EF, EA)
+    np.testing.assert_array_equal(g32, g)
+    np.testing.assert_array_equal(e32, e)
