@@ -297,8 +297,9 @@ eps_status_t run_contract_tma(const Geometry &g, int n_lambda, const void *const
   int x0 = 0, bx = 0;
   support_window(g, &x0, &bx);
   if (bx > TMA_BX_MAX || (g.nz & 1)) return EPS_ERR_UNSUPPORTED;
-  static_assert(sizeof(ContractTmaArgs) < 32000, "kernel parameter space");
-  ContractTmaArgs *ta = new ContractTmaArgs;
+  static_assert(sizeof(ContractTmaArgs) < 8192, "kernel parameter space");
+  ContractTmaArgs targs;
+  ContractTmaArgs *ta = &targs;
   std::memset(ta, 0, sizeof(*ta));
   const long ncol = (long)g.nx * g.ny;
   const size_t comp_bytes = (size_t)ncol * g.nz * 8;
@@ -312,10 +313,8 @@ eps_status_t run_contract_tma(const Geometry &g, int n_lambda, const void *const
       if (enc(&ta->maps[l * 2 + f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
               (void *)(f == 0 ? EF[l] : EA[l]), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
-        delete ta;
+              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return EPS_ERR_UNSUPPORTED;
-      }
     }
     for (int c = 0; c < 3; ++c) ta->fs[l][c] = fs[l][c];
   }
@@ -336,7 +335,6 @@ eps_status_t run_contract_tma(const Geometry &g, int n_lambda, const void *const
     const size_t smem = (size_t)TMA_NSTAGE * 6 * TMA_BY * bx * 4 + 128;
     st = launch("eps_vjp_contract", contract_tma_entry(), dim3((unsigned)blocks), smem, ta, s);
   }
-  delete ta;
   return st;
 }
 
@@ -353,7 +351,7 @@ eps_status_t run_scatter(const Resolved &r, const float *seeds, const float *pd4
   ba.err = err;
   std::memcpy(ba.w, r.w, sizeof(ba.w));
   const KernelEntry k = bwd_entry(r.rp1, r.g.bc);
-  return launch("eps_vjp_scatter", k.fn, bwd_grid(r.g), k.smem, &ba, s);
+  return launch("eps_vjp_scatter", k.fn, bwd_grid(r.g), k.smem, &ba, s, true);
 }
 
 }  // namespace

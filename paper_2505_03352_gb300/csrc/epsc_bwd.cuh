@@ -104,7 +104,10 @@ __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ B
   const int NSTRIP = (GA + NA_B - 1) / NA_B;
   const int DA_USED = NSTRIP * NA_B + 2 * R;   // rows the strips read
 
-  // ---- stage u, the dA/dH seeds and the Sobel seeds ----------------------
+  // everything staged below is written by the stencil kernel queued ahead
+  griddep_wait();
+
+  // ---- stage P' deps / 4, 1/eps^2, the dA/dH seeds and the Sobel seeds ---
   for (int r = ty; r < DA_USED; r += 8) {
     const int va = da_lo + r;
     const bool row_ok = r < DA && (!clamp || (va >= 0 && va < g.mx));

@@ -81,6 +81,10 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
   const int nvi = min(TI, g.nx - i0);
   const int nvj = min(TJ, g.ny - j0);
 
+  // the scatter kernel queued behind this grid may start launching; it
+  // waits for this grid's results before reading them
+  griddep_launch_dependents();
+
   // ---- 1. control tile with halo (asynchronous copies) ----------------
   for (int idx = tid; idx < S::CA * CB; idx += NTHREADS) {
     const int r = idx / CB;
