@@ -155,6 +155,32 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
 eps_status_t eps_sync_status(eps_stream_t stream);
 
 /*
+ * eps_vjp without a caller workspace.  The paper has no counterpart: this
+ * is for host programs that cannot allocate device memory where they need
+ * the gradient (a framework pool that already holds the whole device, or a
+ * loop that must not call cudaMalloc after start-up because it can
+ * synchronise the device).  It allocates nothing: its scratch is one static
+ * device array of EPS_STATIC_WS_BYTES per GPU, created when the library's
+ * device code is loaded on that GPU and held until the process exits.
+ *   - Arguments are those of eps_vjp minus ws / ws_bytes; results are the
+ *     same as eps_vjp's.
+ *   - Problems whose eps_workspace_size() exceeds EPS_STATIC_WS_BYTES are
+ *     rejected with EPS_ERR_WORKSPACE before any launch (about 190 000 Yee
+ *     columns, e.g. 436 x 436).
+ *   - The first call on a device looks up the array's device address (set-up,
+ *     once per device); make that first call before any stream capture.
+ *   - All calls on a device share the one array: calls that can overlap on
+ *     the GPU (different streams, or host threads without ordering) race and
+ *     must be serialised by the caller.  Nothing in the array needs to start
+ *     at zero; it keeps whatever the last call left there.
+ */
+#define EPS_STATIC_WS_BYTES (16 * 1024 * 1024)
+eps_status_t eps_vjp_static(const eps_problem_t *prob, const float *C, int32_t n_lambda,
+                            int32_t field_type, const void *const *EF, const void *const *EA,
+                            const float *field_scales, float scale, float *dJdC, float *eps_out,
+                            eps_stream_t stream);
+
+/*
  * Set the L2 fetch granularity hint (cudaLimitMaxL2FetchGranularity, 0 ..
  * 128 bytes) of the calling thread's current CUDA context and return the
  * previous value in *previous (may be NULL).  The field reads of eps_vjp
