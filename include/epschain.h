@@ -122,10 +122,10 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps,
  *   field_type    eps_field_t of EF / EA
  *   EF, EA        host arrays of n_lambda device pointers, each 16-byte
  *                 aligned.  C64: complex64 [3][nx][ny][nz] (nz even).
- *                 Packed types: the layout eps_field_pack writes.
+ *                 Packed types: buffers written by eps_field_pack.
  *   field_scales  host float [n_lambda][2][3] (wavelength, field F/A,
  *                 component) multiplying each stored component, or NULL
- *                 for all ones; required for the packed types
+ *                 for all ones
  *   dJdC          device, float32 [mx][my], overwritten
  *   eps_out       device float32 [3][nx][ny][nz] or NULL; when given the
  *                 forward eps_hat is written by the same pass (fused
@@ -146,6 +146,31 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
  */
 eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float *G,
                           float *dJdC, void *ws, size_t ws_bytes, eps_stream_t stream);
+
+/*
+ * Reduced-precision field storage (BF16 / FP16 complex pairs with one
+ * scale per component) for eps_vjp's contraction.  A packed field buffer
+ * holds only the planes eps_hat depends on:
+ *   bytes [0, 16)    float scale[3], float pad
+ *   bytes [16, ...)  [3][nx][ny][NP] (re, im) pairs of bf16 or fp16, the
+ *                    planes k0 .. k0+NP-1 of each component divided by its
+ *                    scale, NP = slab_nk + 1 rounded up to a multiple of 4
+ * and decodes as value = scale[c] * stored.  scale = max(|re|, |im|) over
+ * the component's support planes / target (1 for bf16, 2^14 for fp16).
+ * Accumulation in the contraction is FP32.  The reduced precision of the
+ * stored fields is the only source of extra error (stated, not bounded).
+ *
+ * eps_packed_field_bytes: size of one packed field buffer for `prob`.
+ * eps_field_pack: pack one complex64 field [3][nx][ny][nz] (device, 8-byte
+ *   aligned) into `dst` (device, 16-byte aligned, dst_bytes at least
+ *   eps_packed_field_bytes); asynchronous on `stream`.
+ * eps_vjp with field_type EPS_FIELD_BF16X2_SCALED / EPS_FIELD_F16X2_SCALED
+ * takes packed buffers in EF / EA; field_scales (host, optional) multiply
+ * on top of the buffers' own scales.
+ */
+eps_status_t eps_packed_field_bytes(const eps_problem_t *prob, int32_t field_type, size_t *bytes);
+eps_status_t eps_field_pack(const eps_problem_t *prob, int32_t field_type, const void *src,
+                            void *dst, size_t dst_bytes, eps_stream_t stream);
 
 /*
  * Synchronise `stream`, then return (and clear) any device-side error flag

@@ -8,7 +8,7 @@ wraps it as torch.autograd.Functions, `synth` draws the seeded inputs.
 
 from .epschain import (EPS_BC_CLAMP, EPS_BC_PERIODIC, EPS_FIELD_C64, EPS_FIELD_BF16X2_SCALED,
                        EPS_FIELD_F16X2_SCALED, EPS_FLAG_OFFDIAG, EpsError, PreparedVjp, Problem,
-                       eps_forward,
+                       eps_field_pack, eps_forward, eps_packed_field_bytes,
                        eps_profile_start, eps_profile_stop, eps_set_l2_fetch_granularity,
                        eps_status_string, eps_sync_status,
                        eps_vjp, eps_vjp_real, eps_workspace_size, lib)
@@ -16,7 +16,10 @@ from .epschain import (EPS_BC_CLAMP, EPS_BC_PERIODIC, EPS_FIELD_C64, EPS_FIELD_B
 __all__ = [
     "EPS_BC_CLAMP", "EPS_BC_PERIODIC", "EPS_FIELD_C64", "EPS_FIELD_BF16X2_SCALED",
     "EPS_FIELD_F16X2_SCALED", "EPS_FLAG_OFFDIAG", "EpsError", "PreparedVjp", "Problem", "eps_forward",
+    "eps_field_pack", "eps_packed_field_bytes",
     "eps_profile_start", "eps_profile_stop", "eps_set_l2_fetch_granularity", "eps_status_string",
     "eps_sync_status", "eps_vjp",
     "eps_vjp_real", "eps_workspace_size", "lib",
 ]
+
+from . import autograd  # noqa: E402  (torch.autograd wrappers)

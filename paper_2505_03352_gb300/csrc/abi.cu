@@ -15,6 +15,7 @@
 
 #include "epsc_contract.cuh"
 #include "epsc_contract_tma.cuh"
+#include "epsc_pack.cuh"
 #include "epsc_launch.h"
 
 using namespace epsc;
@@ -338,6 +339,38 @@ eps_status_t run_contract_tma(const Geometry &g, int n_lambda, const void *const
   return st;
 }
 
+// Packed planes per column (multiple of 4) and bytes of one packed field.
+int packed_planes(const Geometry &g) { return (g.nk + 1 + 3) & ~3; }
+size_t packed_bytes(const Geometry &g) {
+  return 16 + (size_t)3 * g.nx * g.ny * packed_planes(g) * 4;
+}
+
+eps_status_t run_contract_packed(const Geometry &g, int n_lambda, int type, const void *const *EF,
+                                 const void *const *EA, const float (*fs)[3], float *Wm,
+                                 cudaStream_t s) {
+  ContractPackedArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.nx = g.nx;
+  pa.ny = g.ny;
+  pa.k0 = g.k0;
+  pa.nk = g.nk;
+  pa.np = packed_planes(g);
+  pa.nlambda = n_lambda;
+  pa.type = type;
+  for (int l = 0; l < n_lambda; ++l) {
+    pa.EF[l] = (const unsigned char *)EF[l];
+    pa.EA[l] = (const unsigned char *)EA[l];
+    for (int c = 0; c < 3; ++c) pa.fs[l][c] = fs[l][c];
+  }
+  pa.W = Wm;
+  int nsm = 0;
+  eps_status_t st = sm_count(&nsm);
+  if (st != EPS_OK) return st;
+  const long ncol = (long)g.nx * g.ny;
+  const long blocks = std::max<long>(1, std::min<long>((ncol + NTHREADS - 1) / NTHREADS, (long)nsm * 8));
+  return launch("eps_vjp_contract_packed", contract_packed_entry(), dim3((unsigned)blocks), 0, &pa, s);
+}
+
 eps_status_t run_scatter(const Resolved &r, const float *seeds, const float *pd4, const float *ie2,
                          float *dJdC,
                          int *err, cudaStream_t s) {
@@ -417,7 +450,6 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   if (field_type != EPS_FIELD_C64 && field_type != EPS_FIELD_BF16X2_SCALED &&
       field_type != EPS_FIELD_F16X2_SCALED)
     return EPS_ERR_INVALID_ARG;
-  if (field_type != EPS_FIELD_C64) return EPS_ERR_UNSUPPORTED;
   if (!std::isfinite(scale)) return EPS_ERR_INVALID_ARG;
   if (r.empty) return EPS_OK;
   if (!C || !dJdC) return EPS_ERR_INVALID_ARG;
@@ -429,7 +461,7 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   if (field_scales)
     for (int t = 0; t < 6 * n_lambda; ++t)
       if (!std::isfinite(field_scales[t])) return EPS_ERR_INVALID_ARG;
-  if (r.g.nz & 1) return EPS_ERR_SHAPE;   // complex64 planes are read in pairs
+  if (field_type == EPS_FIELD_C64 && (r.g.nz & 1)) return EPS_ERR_SHAPE;   // planes read in pairs
   if (!aligned(C, 4) || !aligned(dJdC, 4) || (eps_out && !aligned(eps_out, 16)))
     return EPS_ERR_INVALID_ARG;
   if (!ws || !aligned(ws, 256) || ws_bytes < workspace_bytes(r.g)) return EPS_ERR_WORKSPACE;
@@ -465,9 +497,13 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
       ca.fs[l][c] = sc;
     }
   }
-  st = (n_lambda > 0) ? run_contract_tma(r.g, n_lambda, EF, EA, ca.fs, Wm, err, s)
-                      : EPS_ERR_UNSUPPORTED;
-  if (st == EPS_ERR_UNSUPPORTED) st = run_contract(ca, sector_ok ? 4 : 8, s);
+  if (field_type == EPS_FIELD_C64) {
+    st = (n_lambda > 0) ? run_contract_tma(r.g, n_lambda, EF, EA, ca.fs, Wm, err, s)
+                        : EPS_ERR_UNSUPPORTED;
+    if (st == EPS_ERR_UNSUPPORTED) st = run_contract(ca, sector_ok ? 4 : 8, s);
+  } else {
+    st = run_contract_packed(r.g, n_lambda, field_type, EF, EA, ca.fs, Wm, s);
+  }
   if (st != EPS_OK) return st;
 
   // 2. forward chain + seeds (overlaps the contraction until it needs W)
@@ -529,6 +565,56 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
   st = launch("eps_vjp_real_stencil", kf.fn, fwd_grid(r.g), smem, &fa, s, true);
   if (st != EPS_OK) return st;
   return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
+}
+
+eps_status_t eps_packed_field_bytes(const eps_problem_t *prob, int32_t field_type,
+                                    size_t *bytes) {
+  if (!bytes) return EPS_ERR_INVALID_ARG;
+  if (field_type != EPS_FIELD_BF16X2_SCALED && field_type != EPS_FIELD_F16X2_SCALED)
+    return EPS_ERR_INVALID_ARG;
+  Resolved r;
+  eps_status_t st = resolve(prob, &r);
+  if (st != EPS_OK) return st;
+  *bytes = r.empty ? 0 : packed_bytes(r.g);
+  return EPS_OK;
+}
+
+eps_status_t eps_field_pack(const eps_problem_t *prob, int32_t field_type, const void *src,
+                            void *dst, size_t dst_bytes, eps_stream_t stream) {
+  if (field_type != EPS_FIELD_BF16X2_SCALED && field_type != EPS_FIELD_F16X2_SCALED)
+    return EPS_ERR_INVALID_ARG;
+  Resolved r;
+  eps_status_t st = resolve(prob, &r);
+  if (st != EPS_OK) return st;
+  if (r.empty) return EPS_OK;
+  if (!src || !dst) return EPS_ERR_INVALID_ARG;
+  if (!aligned(src, 8) || !aligned(dst, 16)) return EPS_ERR_INVALID_ARG;
+  if (dst_bytes < packed_bytes(r.g)) return EPS_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  PackArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.nx = r.g.nx;
+  pa.ny = r.g.ny;
+  pa.nz = r.g.nz;
+  pa.k0 = r.g.k0;
+  pa.nk = r.g.nk;
+  pa.np = packed_planes(r.g);
+  pa.type = field_type;
+  pa.src = (const float2 *)src;
+  pa.dst = (unsigned char *)dst;
+  int nsm = 0;
+  if ((st = sm_count(&nsm)) != EPS_OK) return st;
+  if (cudaMemsetAsync(dst, 0, 16, s) != cudaSuccess) return EPS_ERR_CUDA;
+  if ((st = launch("eps_field_pack_amax", pack_amax_entry(), dim3((unsigned)nsm * 2, 3), 0, &pa,
+                   s)) != EPS_OK)
+    return st;
+  if ((st = launch("eps_field_pack", pack_entry(), dim3((unsigned)nsm * 8), 0, &pa, s)) != EPS_OK)
+    return st;
+  unsigned char *d = (unsigned char *)dst;
+  void *args[] = {&d, &pa.type};
+  if (cudaLaunchKernel(pack_finish_entry(), dim3(1), dim3(32), args, 0, s) != cudaSuccess)
+    return EPS_ERR_CUDA;
+  return EPS_OK;
 }
 
 eps_status_t eps_sync_status(eps_stream_t stream) {

@@ -24,6 +24,12 @@ const void *contract_entry(int lanes);
 // Contraction kernel fed by bulk tensor copies (complex64 fields).
 const void *contract_tma_entry();
 
+// Reduced-precision field path.
+const void *pack_amax_entry();
+const void *pack_entry();
+const void *pack_finish_entry();
+const void *contract_packed_entry();
+
 inline KernelEntry fwd_entry(int rp1, int bc) {
   return rp1 <= 6 ? fwd_entry_a(rp1, bc) : fwd_entry_b(rp1, bc);
 }

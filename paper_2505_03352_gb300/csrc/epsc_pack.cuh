@@ -1,0 +1,168 @@
+// Reduced-precision field storage for the Eq. 1 contraction.
+//
+// Packed field buffer (one per wavelength and per forward/adjoint field):
+//   bytes [0, 16)   float scale[3] (one per component) and one float of pad
+//   bytes [16, ...) [3][nx][ny][NP] elements, each an (re, im) pair of bf16
+//                   or fp16 (4 bytes), holding planes k0 .. k0 + NP - 1 of
+//                   the component divided by its scale; NP = nk + 1 rounded
+//                   up to a multiple of 4 (planes past nz are zero).
+// So a packed field holds exactly the J-support planes, contiguous per
+// column, and decodes as value = scale[c] * stored.  The scale of a
+// component is max(|re|, |im|) over its support planes divided by the
+// format's target magnitude (1 for bf16, 2^14 for fp16), or 1 if that max
+// is 0.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "epsc_common.cuh"
+
+namespace epsc {
+
+constexpr float BF16_TARGET = 1.0f;
+constexpr float F16_TARGET = 16384.0f;
+
+struct PackArgs {
+  int nx, ny, nz, k0, nk, np;   // np: packed planes per column (multiple of 4)
+  int type;                     // EPS_FIELD_BF16X2_SCALED or EPS_FIELD_F16X2_SCALED
+  const float2 *src;            // complex64 [3][nx][ny][nz]
+  unsigned char *dst;           // packed buffer
+};
+
+struct ContractPackedArgs {
+  int nx, ny, k0, nk, np, nlambda, type;
+  const unsigned char *EF[EPS_MAX_LAMBDA];
+  const unsigned char *EA[EPS_MAX_LAMBDA];
+  float fs[EPS_MAX_LAMBDA][3];   // scale * extra caller factors
+  float *W;                      // [4][nx][ny]
+};
+
+// The kernels below are compiled in one translation unit only.
+#ifdef EPSC_PACK_KERNELS
+
+// max |re|, |im| over the support planes of each component, into the
+// header (as float bits, non-negative floats order like their bit patterns)
+__global__ void __launch_bounds__(NTHREADS) pack_amax_kernel(const __grid_constant__ PackArgs a) {
+  const long ncol = (long)a.nx * a.ny;
+  unsigned *hdr = reinterpret_cast<unsigned *>(a.dst);
+  const int c = blockIdx.y;
+  float m = 0.f;
+  const long total = ncol * (a.nk + 1);
+  for (long t = (long)blockIdx.x * NTHREADS + threadIdx.x; t < total; t += (long)gridDim.x * NTHREADS) {
+    const long col = t / (a.nk + 1);
+    const int k = a.k0 + (int)(t - col * (a.nk + 1));
+    const float2 v = a.src[((size_t)c * ncol + col) * a.nz + k];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(hdr + c, __float_as_uint(m));
+}
+
+// convert the header maxima to scales, then write the packed planes
+__global__ void __launch_bounds__(NTHREADS) pack_kernel(const __grid_constant__ PackArgs a) {
+  const long ncol = (long)a.nx * a.ny;
+  const float *hdr = reinterpret_cast<const float *>(a.dst);
+  const float target = a.type == EPS_FIELD_BF16X2_SCALED ? BF16_TARGET : F16_TARGET;
+  const long total = 3 * ncol * a.np;
+  unsigned *out = reinterpret_cast<unsigned *>(a.dst + 16);
+  for (long t = (long)blockIdx.x * NTHREADS + threadIdx.x; t < total; t += (long)gridDim.x * NTHREADS) {
+    const long cc = t / a.np;               // component * ncol + column
+    const int kk = (int)(t - cc * a.np);
+    const int c = (int)(cc / ncol);
+    const float amax = hdr[c];
+    const float inv = amax > 0.f ? target / amax : 1.f;
+    const int k = a.k0 + kk;
+    float2 v = make_float2(0.f, 0.f);
+    if (kk <= a.nk && k < a.nz) v = a.src[(size_t)cc * a.nz + k];
+    unsigned bits;
+    if (a.type == EPS_FIELD_BF16X2_SCALED) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v.x * inv, v.y * inv);
+      bits = *reinterpret_cast<const unsigned *>(&h);
+    } else {
+      const __half2 h = __floats2half2_rn(v.x * inv, v.y * inv);
+      bits = *reinterpret_cast<const unsigned *>(&h);
+    }
+    out[t] = bits;
+  }
+}
+
+// header maxima -> scales (one thread per component), after pack_kernel
+__global__ void pack_finish_kernel(unsigned char *dst, int type) {
+  float *hdr = reinterpret_cast<float *>(dst);
+  const int c = threadIdx.x;
+  if (c < 3) {
+    const float target = type == EPS_FIELD_BF16X2_SCALED ? BF16_TARGET : F16_TARGET;
+    const float amax = hdr[c];
+    hdr[c] = amax > 0.f ? amax / target : 1.f;
+  }
+}
+
+__device__ __forceinline__ float2 unpack2(unsigned bits, int type) {
+  if (type == EPS_FIELD_BF16X2_SCALED) {
+    __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&bits);
+    return __bfloat1622float2(h);
+  }
+  __half2 h = *reinterpret_cast<const __half2 *>(&bits);
+  return __half22float2(h);
+}
+
+// Contraction over packed fields: one thread per column and wavelength
+// pass, 16-byte loads of four packed planes at a time, FP32 accumulation.
+__global__ void __launch_bounds__(NTHREADS) contract_packed_kernel(const __grid_constant__ ContractPackedArgs a) {
+  griddep_launch_dependents();
+  const long ncol = (long)a.nx * a.ny;
+  const int nq = a.np >> 2;   // uint4 per column and component
+  for (long col = (long)blockIdx.x * NTHREADS + threadIdx.x; col < ncol; col += (long)gridDim.x * NTHREADS) {
+    float wx = 0.f, wy = 0.f, wzi = 0.f, wzf = 0.f;
+    for (int l = 0; l < a.nlambda; ++l) {
+      const float *hf = reinterpret_cast<const float *>(a.EF[l]);
+      const float *ha = reinterpret_cast<const float *>(a.EA[l]);
+      const uint4 *pf = reinterpret_cast<const uint4 *>(a.EF[l] + 16);
+      const uint4 *pa = reinterpret_cast<const uint4 *>(a.EA[l] + 16);
+      float sums[4] = {0.f, 0.f, 0.f, 0.f};   // x, y, z interior, z faces (unscaled)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const size_t base = ((size_t)c * ncol + col) * nq;
+        float s_in = 0.f, s_face = 0.f;
+        for (int q = 0; q < nq; ++q) {
+          const uint4 f = __ldg(pf + base + q);
+          const uint4 e = __ldg(pa + base + q);
+          const unsigned fb[4] = {f.x, f.y, f.z, f.w};
+          const unsigned eb[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int kk = 4 * q + t;   // packed plane kk is plane k0 + kk
+            const float2 x = unpack2(fb[t], a.type);
+            const float2 y = unpack2(eb[t], a.type);
+            const float re = fmaf(x.x, y.x, -x.y * y.y);
+            const bool in = c < 2 ? (kk >= 1 && kk <= a.nk) : (kk >= 1 && kk <= a.nk - 1);
+            const bool face = c == 2 && (kk == 0 || kk == a.nk);
+            s_in += in ? re : 0.f;
+            s_face += face ? re : 0.f;
+          }
+        }
+        const float sc = __ldg(hf + c) * __ldg(ha + c) * a.fs[l][c];
+        if (c < 2) {
+          sums[c] = s_in * sc;
+        } else {
+          sums[2] = s_in * sc;
+          sums[3] = s_face * sc;
+        }
+      }
+      wx += sums[0];
+      wy += sums[1];
+      wzi += sums[2];
+      wzf += sums[3];
+    }
+    a.W[0 * ncol + col] = wx;
+    a.W[1 * ncol + col] = wy;
+    a.W[2 * ncol + col] = wzi;
+    a.W[3 * ncol + col] = wzf;
+  }
+}
+
+#endif  // EPSC_PACK_KERNELS
+
+}  // namespace epsc

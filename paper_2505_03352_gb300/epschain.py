@@ -98,6 +98,10 @@ _PROTOS = {
     "eps_vjp_real": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP,
                                     ctypes.c_size_t, _VP]),
     "eps_sync_status": (ctypes.c_int, [_VP]),
+    "eps_packed_field_bytes": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_size_t)]),
+    "eps_field_pack": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), ctypes.c_int32, _VP, _VP,
+                                      ctypes.c_size_t, _VP]),
     "eps_profile_start": (ctypes.c_int, []),
     "eps_set_l2_fetch_granularity": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "eps_profile_stop": (ctypes.c_int, [ctypes.POINTER(eps_profile_entry_t), ctypes.c_int32,
@@ -206,6 +210,12 @@ def eps_vjp(prob: Problem, C, EF, EA, scale: float = -2.0, dJdC=None, eps_out=No
         for l in range(nl):
             _need(EF[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EF[{l}]")
             _need(EA[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EA[{l}]")
+    else:
+        nbytes = eps_packed_field_bytes(prob, field_type)
+        for l in range(nl):
+            for name, t in ((f"EF[{l}]", EF[l]), (f"EA[{l}]", EA[l])):
+                if not (t.is_cuda and t.dtype == torch.uint8 and t.numel() >= nbytes):
+                    raise ValueError(f"{name} must be a packed field buffer of {nbytes} bytes")
     if dJdC is None:
         dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=C.device)
     _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC")
@@ -254,6 +264,29 @@ def eps_vjp_real(prob: Problem, C, G, dJdC=None, ws=None, stream=None):
     _check(lib().eps_vjp_real(ctypes.byref(p), _ptr(C), _ptr(G), _ptr(dJdC), _ptr(ws), ws.numel(),
                               _stream(stream)), "eps_vjp_real")
     return dJdC
+
+
+def eps_packed_field_bytes(prob: Problem, field_type: int) -> int:
+    n = ctypes.c_size_t(0)
+    p = prob.c_struct()
+    _check(lib().eps_packed_field_bytes(ctypes.byref(p), field_type, ctypes.byref(n)),
+           "eps_packed_field_bytes")
+    return n.value
+
+
+def eps_field_pack(prob: Problem, field_type: int, E, out=None, stream=None):
+    """Pack one complex64 field [3, nx, ny, nz] into the reduced-precision
+    buffer format eps_vjp accepts for EPS_FIELD_BF16X2_SCALED /
+    EPS_FIELD_F16X2_SCALED (uint8 device tensor; see include/epschain.h)."""
+    import torch
+    _need(E, (3, prob.nx, prob.ny, prob.nz), torch.complex64, "E")
+    nbytes = eps_packed_field_bytes(prob, field_type)
+    if out is None:
+        out = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=E.device)
+    p = prob.c_struct()
+    _check(lib().eps_field_pack(ctypes.byref(p), field_type, _ptr(E), _ptr(out), out.numel(),
+                                _stream(stream)), "eps_field_pack")
+    return out
 
 
 def eps_sync_status(stream=None):
