@@ -65,6 +65,8 @@ typedef enum {
 #define EPS_FLAG_OFFDIAG 1  /* eps_forward also writes the xy inverse-permittivity term */
 
 #define EPS_MAX_LAMBDA 16    /* wavelengths per eps_vjp call */
+#define EPS_MAX_BATCH 64     /* regions per batched call */
+#define EPS_MAX_BATCH_LAMBDA 4 /* wavelengths per region in a batched call */
 #define EPS_MAX_RADIUS 12.0f /* largest conic filter radius (subpixels) */
 
 /*
@@ -146,6 +148,29 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
  */
 eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float *G,
                           float *dJdC, void *ws, size_t ws_bytes, eps_stream_t stream);
+
+/*
+ * Batched calls: n <= EPS_MAX_BATCH independent design regions, each with
+ * its own eps_problem_t (sizes, radius, beta, slab, boundary rule), in one
+ * call.  Host arrays of n device pointers (C, eps / dJdC / eps_out); EF and
+ * EA are host arrays of n * n_lambda device pointers, region-major
+ * (EF[k * n_lambda + l]); field_scales, if not NULL, is host float
+ * [n][n_lambda][2][3].  n_lambda <= EPS_MAX_BATCH_LAMBDA; complex64 fields
+ * only; eps_out may be NULL or hold NULL entries.  The workspace is the
+ * regions' eps_workspace_size() laid end to end (eps_batched_workspace_size).
+ * One contraction launch covers every region; regions that share a filter
+ * radius and boundary rule share one stencil and one scatter launch (tiles
+ * of the largest regions first).  Results equal the per-region calls'.
+ */
+eps_status_t eps_batched_workspace_size(int32_t n, const eps_problem_t *probs, int32_t n_lambda,
+                                        size_t *bytes);
+eps_status_t eps_forward_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
+                                 float *const *eps, eps_stream_t stream);
+eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
+                             int32_t n_lambda, int32_t field_type, const void *const *EF,
+                             const void *const *EA, const float *field_scales, float scale,
+                             float *const *dJdC, float *const *eps_out, void *ws, size_t ws_bytes,
+                             eps_stream_t stream);
 
 /*
  * Reduced-precision field storage (BF16 / FP16 complex pairs with one

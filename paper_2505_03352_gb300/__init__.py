@@ -6,7 +6,8 @@ The CUDA kernels live in csrc/ behind the C ABI of include/epschain.h;
 wraps it as torch.autograd.Functions, `synth` draws the seeded inputs.
 """
 
-from .epschain import (EPS_BC_CLAMP, EPS_BC_PERIODIC, EPS_FIELD_C64, EPS_FIELD_BF16X2_SCALED,
+from .epschain import (BatchedVjp, eps_batched_workspace_size, eps_forward_batched,
+                       EPS_BC_CLAMP, EPS_BC_PERIODIC, EPS_FIELD_C64, EPS_FIELD_BF16X2_SCALED,
                        EPS_FIELD_F16X2_SCALED, EPS_FLAG_OFFDIAG, EpsError, PreparedVjp, Problem,
                        eps_field_pack, eps_forward, eps_packed_field_bytes,
                        eps_profile_start, eps_profile_stop, eps_set_l2_fetch_granularity,
@@ -14,6 +15,7 @@ from .epschain import (EPS_BC_CLAMP, EPS_BC_PERIODIC, EPS_FIELD_C64, EPS_FIELD_B
                        eps_vjp, eps_vjp_real, eps_workspace_size, lib)
 
 __all__ = [
+    "BatchedVjp", "eps_batched_workspace_size", "eps_forward_batched",
     "EPS_BC_CLAMP", "EPS_BC_PERIODIC", "EPS_FIELD_C64", "EPS_FIELD_BF16X2_SCALED",
     "EPS_FIELD_F16X2_SCALED", "EPS_FLAG_OFFDIAG", "EpsError", "PreparedVjp", "Problem", "eps_forward",
     "eps_field_pack", "eps_packed_field_bytes",

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -233,8 +234,8 @@ size_t fwd_smem(const KernelEntry &k, const Geometry &g, int ncomp, int *stage_f
 
 void fill_fwd_common(FwdArgs &fa, const Resolved &r, const float *C, int *err) {
   std::memset(&fa, 0, sizeof(fa));
-  fa.g = r.g;
-  fa.C = C;
+  fa.r.g = r.g;
+  fa.r.C = C;
   fa.err = err;
   std::memcpy(fa.w, r.w, sizeof(fa.w));
 }
@@ -376,11 +377,11 @@ eps_status_t run_scatter(const Resolved &r, const float *seeds, const float *pd4
                          int *err, cudaStream_t s) {
   BwdArgs ba;
   std::memset(&ba, 0, sizeof(ba));
-  ba.g = r.g;
-  ba.seeds = seeds;
-  ba.pd4 = pd4;
-  ba.ie2 = ie2;
-  ba.dJdC = dJdC;
+  ba.r.g = r.g;
+  ba.r.seeds = seeds;
+  ba.r.pd4 = pd4;
+  ba.r.ie2 = ie2;
+  ba.r.dJdC = dJdC;
   ba.err = err;
   std::memcpy(ba.w, r.w, sizeof(ba.w));
   const KernelEntry k = bwd_entry(r.rp1, r.g.bc);
@@ -429,13 +430,13 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps, 
   if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
   FwdArgs fa;
   fill_fwd_common(fa, r, C, err);
-  fa.mode = MODE_FWD;
-  fa.write_eps = 1;
-  fa.write_offdiag = od ? 1 : 0;
-  fa.eps = eps;
-  fa.offdiag = od ? offdiag : nullptr;
+  fa.r.mode = MODE_FWD;
+  fa.r.write_eps = 1;
+  fa.r.write_offdiag = od ? 1 : 0;
+  fa.r.eps = eps;
+  fa.r.offdiag = od ? offdiag : nullptr;
   const KernelEntry k = fwd_entry(r.rp1, r.g.bc);
-  const size_t smem = fwd_smem(k, r.g, od ? 5 : 3, &fa.stage_floats);
+  const size_t smem = fwd_smem(k, r.g, od ? 5 : 3, &fa.r.stage_floats);
   return launch("eps_forward", k.fn, fwd_grid(r.g), smem, &fa, (cudaStream_t)stream);
 }
 
@@ -509,15 +510,15 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   // 2. forward chain + seeds (overlaps the contraction until it needs W)
   FwdArgs fa;
   fill_fwd_common(fa, r, C, err);
-  fa.mode = MODE_C64;
-  fa.write_eps = eps_out ? 1 : 0;
-  fa.eps = eps_out;
-  fa.W = Wm;
-  fa.seeds = seeds;
-  fa.pd4 = pd4;
-  fa.ie2 = ie2;
+  fa.r.mode = MODE_C64;
+  fa.r.write_eps = eps_out ? 1 : 0;
+  fa.r.eps = eps_out;
+  fa.r.W = Wm;
+  fa.r.seeds = seeds;
+  fa.r.pd4 = pd4;
+  fa.r.ie2 = ie2;
   const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
-  const size_t smem = fwd_smem(kf, r.g, eps_out ? 3 : 0, &fa.stage_floats);
+  const size_t smem = fwd_smem(kf, r.g, eps_out ? 3 : 0, &fa.r.stage_floats);
   st = launch(eps_out ? "eps_fwd_vjp_stencil" : "eps_vjp_stencil", kf.fn, fwd_grid(r.g), smem,
               &fa, s, true);
   if (st != EPS_OK) return st;
@@ -555,13 +556,13 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
   if ((st = run_contract(ca, 8, s)) != EPS_OK) return st;
   FwdArgs fa;
   fill_fwd_common(fa, r, C, err);
-  fa.mode = MODE_REAL;
-  fa.W = Wm;
-  fa.seeds = seeds;
-  fa.pd4 = pd4;
-  fa.ie2 = ie2;
+  fa.r.mode = MODE_REAL;
+  fa.r.W = Wm;
+  fa.r.seeds = seeds;
+  fa.r.pd4 = pd4;
+  fa.r.ie2 = ie2;
   const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
-  const size_t smem = fwd_smem(kf, r.g, 0, &fa.stage_floats);
+  const size_t smem = fwd_smem(kf, r.g, 0, &fa.r.stage_floats);
   st = launch("eps_vjp_real_stencil", kf.fn, fwd_grid(r.g), smem, &fa, s, true);
   if (st != EPS_OK) return st;
   return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
@@ -682,6 +683,264 @@ eps_status_t eps_profile_stop(eps_profile_entry_t *entries, int32_t max_entries,
   for (size_t t = 0; t < agg.size() && entries && n < max_entries; ++t) entries[n++] = agg[t];
   if (n_entries) *n_entries = n;
   return st;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- batched calls
+
+namespace {
+
+// Regions that share one conic filter and boundary rule run in one batched
+// stencil launch and one batched scatter launch.
+struct Group {
+  int rp1, bc;
+  float radius;
+  std::vector<int> regions;   // indices, largest tile count first
+};
+
+eps_status_t resolve_batch(int32_t n, const eps_problem_t *probs, std::vector<Resolved> &rs,
+                           std::vector<size_t> &ws_off, size_t *ws_total) {
+  if (n < 0 || n > EPS_MAX_BATCH || (n > 0 && !probs)) return EPS_ERR_INVALID_ARG;
+  rs.resize(n);
+  ws_off.resize(n);
+  size_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    eps_status_t st = resolve(&probs[k], &rs[k]);
+    if (st != EPS_OK) return st;
+    ws_off[k] = off;
+    off += rs[k].empty ? 0 : workspace_bytes(rs[k].g);
+  }
+  *ws_total = off;
+  return EPS_OK;
+}
+
+std::vector<Group> make_groups(const std::vector<Resolved> &rs, const eps_problem_t *probs) {
+  std::vector<Group> gs;
+  for (int k = 0; k < (int)rs.size(); ++k) {
+    if (rs[k].empty) continue;
+    size_t gi = 0;
+    for (; gi < gs.size(); ++gi)
+      if (gs[gi].rp1 == rs[k].rp1 && gs[gi].bc == rs[k].g.bc && gs[gi].radius == probs[k].radius)
+        break;
+    if (gi == gs.size()) gs.push_back(Group{rs[k].rp1, rs[k].g.bc, probs[k].radius, {}});
+    gs[gi].regions.push_back(k);
+  }
+  auto tiles = [&](int k) { return (long)fwd_grid(rs[k].g).x * fwd_grid(rs[k].g).y; };
+  for (Group &g : gs)
+    std::stable_sort(g.regions.begin(), g.regions.end(),
+                     [&](int x, int y) { return tiles(x) > tiles(y); });
+  return gs;
+}
+
+// One batched stencil launch per group (forward-only or VJP mode).
+eps_status_t run_fwd_batched(const std::vector<Group> &gs, const std::vector<Resolved> &rs,
+                             const std::vector<FwdRegion> &regions, int ncomp, int *err,
+                             cudaStream_t s, bool pdl) {
+  FwdBatchArgs *ba = new FwdBatchArgs;
+  eps_status_t st = EPS_OK;
+  for (const Group &g : gs) {
+    std::memset(ba, 0, sizeof(*ba));
+    ba->n = (int)g.regions.size();
+    ba->err = err;
+    std::memcpy(ba->w, rs[g.regions[0]].w, sizeof(ba->w));
+    const KernelEntry k = fwd_entry(g.rp1, g.bc, true);
+    size_t smem = 0;
+    int tiles = 0;
+    for (int q = 0; q < ba->n; ++q) {
+      const int ri = g.regions[q];
+      int sf = 0;
+      smem = std::max(smem, fwd_smem(k, rs[ri].g, ncomp, &sf));
+      const dim3 grid = fwd_grid(rs[ri].g);
+      ba->tile_start[q] = tiles;
+      ba->tiles_j[q] = (int)grid.x;
+      tiles += (int)(grid.x * grid.y);
+      ba->r[q] = regions[ri];
+    }
+    ba->tile_start[ba->n] = tiles;
+    for (int q = 0; q < ba->n; ++q) ba->r[q].stage_floats = (int)(smem / sizeof(float));
+    st = launch("eps_batched_stencil", k.fn, dim3((unsigned)tiles), smem, ba, s, pdl);
+    if (st != EPS_OK) break;
+  }
+  delete ba;
+  return st;
+}
+
+eps_status_t run_bwd_batched(const std::vector<Group> &gs, const std::vector<Resolved> &rs,
+                             const std::vector<BwdRegion> &regions, int *err, cudaStream_t s) {
+  BwdBatchArgs *ba = new BwdBatchArgs;
+  eps_status_t st = EPS_OK;
+  for (const Group &g : gs) {
+    std::memset(ba, 0, sizeof(*ba));
+    ba->n = (int)g.regions.size();
+    ba->err = err;
+    std::memcpy(ba->w, rs[g.regions[0]].w, sizeof(ba->w));
+    const KernelEntry k = bwd_entry(g.rp1, g.bc, true);
+    int tiles = 0;
+    for (int q = 0; q < ba->n; ++q) {
+      const int ri = g.regions[q];
+      const dim3 grid = bwd_grid(rs[ri].g);
+      ba->tile_start[q] = tiles;
+      ba->tiles_j[q] = (int)grid.x;
+      tiles += (int)(grid.x * grid.y);
+      ba->r[q] = regions[ri];
+    }
+    ba->tile_start[ba->n] = tiles;
+    st = launch("eps_batched_scatter", k.fn, dim3((unsigned)tiles), k.smem, ba, s, true);
+    if (st != EPS_OK) break;
+  }
+  delete ba;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+eps_status_t eps_batched_workspace_size(int32_t n, const eps_problem_t *probs, int32_t n_lambda,
+                                        size_t *bytes) {
+  if (!bytes) return EPS_ERR_INVALID_ARG;
+  if (n_lambda < 0 || n_lambda > EPS_MAX_BATCH_LAMBDA) return EPS_ERR_INVALID_ARG;
+  std::vector<Resolved> rs;
+  std::vector<size_t> off;
+  return resolve_batch(n, probs, rs, off, bytes);
+}
+
+eps_status_t eps_forward_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
+                                 float *const *eps, eps_stream_t stream) {
+  std::vector<Resolved> rs;
+  std::vector<size_t> off;
+  size_t total = 0;
+  eps_status_t st = resolve_batch(n, probs, rs, off, &total);
+  if (st != EPS_OK) return st;
+  if (n == 0) return EPS_OK;
+  if (!C || !eps) return EPS_ERR_INVALID_ARG;
+  std::vector<FwdRegion> regions(n);
+  for (int k = 0; k < n; ++k) {
+    if (rs[k].empty) continue;
+    if (probs[k].flags & EPS_FLAG_OFFDIAG) return EPS_ERR_UNSUPPORTED;
+    if (!C[k] || !eps[k] || !aligned(C[k], 4) || !aligned(eps[k], 16)) return EPS_ERR_INVALID_ARG;
+    std::memset(&regions[k], 0, sizeof(FwdRegion));
+    regions[k].g = rs[k].g;
+    regions[k].mode = MODE_FWD;
+    regions[k].write_eps = 1;
+    regions[k].C = C[k];
+    regions[k].eps = eps[k];
+  }
+  int *err = nullptr;
+  if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
+  const std::vector<Group> gs = make_groups(rs, probs);
+  return run_fwd_batched(gs, rs, regions, 3, err, (cudaStream_t)stream, false);
+}
+
+eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
+                             int32_t n_lambda, int32_t field_type, const void *const *EF,
+                             const void *const *EA, const float *field_scales, float scale,
+                             float *const *dJdC, float *const *eps_out, void *ws, size_t ws_bytes,
+                             eps_stream_t stream) {
+  std::vector<Resolved> rs;
+  std::vector<size_t> off;
+  size_t total = 0;
+  eps_status_t st = resolve_batch(n, probs, rs, off, &total);
+  if (st != EPS_OK) return st;
+  if (n_lambda < 0 || n_lambda > EPS_MAX_BATCH_LAMBDA) return EPS_ERR_INVALID_ARG;
+  if (field_type != EPS_FIELD_C64) {
+    if (field_type == EPS_FIELD_BF16X2_SCALED || field_type == EPS_FIELD_F16X2_SCALED)
+      return EPS_ERR_UNSUPPORTED;
+    return EPS_ERR_INVALID_ARG;
+  }
+  if (!std::isfinite(scale)) return EPS_ERR_INVALID_ARG;
+  if (n == 0) return EPS_OK;
+  if (!C || !dJdC || (n_lambda > 0 && (!EF || !EA))) return EPS_ERR_INVALID_ARG;
+  if (!ws || !aligned(ws, 256) || ws_bytes < total) return EPS_ERR_WORKSPACE;
+  int *err = nullptr;
+  if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
+
+  ContractBatchArgs *ca = new ContractBatchArgs;
+  std::memset(ca, 0, sizeof(*ca));
+  std::vector<FwdRegion> fr(n);
+  std::vector<BwdRegion> br(n);
+  long ncol = 0;
+  for (int k = 0; k < n; ++k) {
+    std::memset(&fr[k], 0, sizeof(FwdRegion));
+    std::memset(&br[k], 0, sizeof(BwdRegion));
+    if (rs[k].empty) continue;
+    const Geometry &g = rs[k].g;
+    float *out_eps = eps_out ? eps_out[k] : nullptr;
+    if (!C[k] || !dJdC[k] || !aligned(C[k], 4) || !aligned(dJdC[k], 4) ||
+        (out_eps && !aligned(out_eps, 16)) || (g.nz & 1)) {
+      delete ca;
+      return (g.nz & 1) ? EPS_ERR_SHAPE : EPS_ERR_INVALID_ARG;
+    }
+    const WsLayout L = ws_layout(g);
+    char *base = (char *)ws + off[k];
+    float *Wm = (float *)(base + L.w);
+    float *seeds = (float *)(base + L.seeds);
+    float *pd4 = (float *)(base + L.pd4);
+    float *ie2 = (float *)(base + L.ie2);
+    ContractBatchRegion &cr = ca->r[ca->n++];
+    cr.col_start = ncol;
+    cr.nz = g.nz;
+    cr.k0 = g.k0;
+    cr.nk = g.nk;
+    cr.nlambda = n_lambda;
+    cr.W = Wm;
+    for (int l = 0; l < n_lambda; ++l) {
+      const void *ef = EF[k * n_lambda + l], *ea = EA[k * n_lambda + l];
+      if (!ef || !ea || !aligned(ef, 16) || !aligned(ea, 16)) {
+        delete ca;
+        return EPS_ERR_INVALID_ARG;
+      }
+      cr.EF[l] = (const float *)ef;
+      cr.EA[l] = (const float *)ea;
+      for (int c = 0; c < 3; ++c) {
+        float sc = scale;
+        if (field_scales) {
+          const float *fsr = field_scales + (size_t)(k * n_lambda + l) * 6;
+          sc *= fsr[c] * fsr[3 + c];
+          if (!std::isfinite(sc)) {
+            delete ca;
+            return EPS_ERR_INVALID_ARG;
+          }
+        }
+        cr.fs[l][c] = sc;
+      }
+    }
+    ncol += (long)g.nx * g.ny;
+    fr[k].g = g;
+    fr[k].mode = MODE_C64;
+    fr[k].write_eps = out_eps ? 1 : 0;
+    fr[k].C = C[k];
+    fr[k].eps = out_eps;
+    fr[k].W = Wm;
+    fr[k].seeds = seeds;
+    fr[k].pd4 = pd4;
+    fr[k].ie2 = ie2;
+    br[k].g = g;
+    br[k].seeds = seeds;
+    br[k].pd4 = pd4;
+    br[k].ie2 = ie2;
+    br[k].dJdC = dJdC[k];
+  }
+  ca->ncol = ncol;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ncol > 0) {
+    int nsm = 0;
+    if ((st = sm_count(&nsm)) != EPS_OK) {
+      delete ca;
+      return st;
+    }
+    const long per_block = (NTHREADS / 32) * 4;
+    const long blocks = std::max<long>(1, std::min<long>((ncol + per_block - 1) / per_block, (long)nsm * 8));
+    st = launch("eps_batched_contract", contract_batched_entry(), dim3((unsigned)blocks), 0, ca, s);
+  }
+  delete ca;
+  if (st != EPS_OK) return st;
+  const std::vector<Group> gs = make_groups(rs, probs);
+  bool any_eps = false;
+  for (int k = 0; k < n; ++k) any_eps = any_eps || (eps_out && eps_out[k]);
+  if ((st = run_fwd_batched(gs, rs, fr, any_eps ? 3 : 0, err, s, true)) != EPS_OK) return st;
+  return run_bwd_batched(gs, rs, br, err, s);
 }
 
 }  // extern "C"

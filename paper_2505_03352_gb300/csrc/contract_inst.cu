@@ -10,6 +10,8 @@ const void *contract_entry(int lanes) {
   return lanes == 4 ? (const void *)&contract_kernel<4> : (const void *)&contract_kernel<8>;
 }
 
+const void *contract_batched_entry() { return (const void *)&contract_batched_kernel<0>; }
+
 const void *contract_tma_entry() { return (const void *)&contract_tma_kernel<TMA_NSTAGE>; }
 
 }  // namespace epsc

@@ -68,8 +68,10 @@ __device__ __forceinline__ void sobel_t_weights(int t, int n, int bc, float (&wd
   }
 }
 
-template <int RP1, int BC>
-__global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ BwdArgs a) {
+// One tile (subpixel rows a0 .., columns b0 ..) of one region `rg`.
+template <int RP1, int BC, class Args>
+__device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, const int a0,
+                                         const int b0) {
   using S = BwdSmem<RP1>;
   constexpr int R = S::R;
   constexpr int DBP = S::DBP;
@@ -82,10 +84,9 @@ __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ B
   float *sdU = smem + S::OFF_DU;
   float *sdc = smem + S::OFF_DCE;
 
-  const Geometry &g = a.g;
+  const Geometry &g = rg.g;
   const int tid = threadIdx.x;
   const int ty = tid >> 5, tx = tid & 31;       // 8 x 32 thread grid for 2-D loops
-  const int a0 = blockIdx.y * TA, b0 = blockIdx.x * TB;
   const int aend = min(a0 + TA, g.mx), bend = min(b0 + TB, g.my);
   // gather region: the tile, plus R extended positions where edge replicate folds
   const int ga_lo = a0 - ((clamp && a0 == 0) ? R : 0);
@@ -116,8 +117,8 @@ __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ B
       const int vb = db_lo + c;
       const bool ok = row_ok && (!clamp || (vb >= 0 && vb < g.my));
       const size_t o = ok ? rowo + (clamp ? vb : wrapi(vb, g.my)) : 0;
-      cp_async4(sU + r * DBP + c, a.pd4 + o, ok);
-      cp_async4(sIE2 + r * DBP + c, a.ie2 + o, ok);
+      cp_async4(sU + r * DBP + c, rg.pd4 + o, ok);
+      cp_async4(sIE2 + r * DBP + c, rg.ie2 + o, ok);
     }
   }
   for (int r = ty; r < NCI; r += 8) {
@@ -129,12 +130,12 @@ __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ B
       const bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
       const size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
       float *d = sSeed + r * S::NCJ + c;
-      cp_async4(d + 0 * S::NC, a.seeds + S_DAX * plane + o, ok);
-      cp_async4(d + 1 * S::NC, a.seeds + S_DHX * plane + o, ok);
-      cp_async4(d + 2 * S::NC, a.seeds + S_DAY * plane + o, ok);
-      cp_async4(d + 3 * S::NC, a.seeds + S_DHY * plane + o, ok);
-      cp_async4(d + 4 * S::NC, a.seeds + S_DAZ * plane + o, ok);
-      cp_async4(d + 5 * S::NC, a.seeds + S_DHZ * plane + o, ok);
+      cp_async4(d + 0 * S::NC, rg.seeds + S_DAX * plane + o, ok);
+      cp_async4(d + 1 * S::NC, rg.seeds + S_DHX * plane + o, ok);
+      cp_async4(d + 2 * S::NC, rg.seeds + S_DAY * plane + o, ok);
+      cp_async4(d + 3 * S::NC, rg.seeds + S_DHY * plane + o, ok);
+      cp_async4(d + 4 * S::NC, rg.seeds + S_DAZ * plane + o, ok);
+      cp_async4(d + 5 * S::NC, rg.seeds + S_DHZ * plane + o, ok);
     }
   }
   for (int r = ty; r < NCI + 2; r += 8) {
@@ -146,10 +147,10 @@ __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ B
       const bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
       const size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
       float *d = sG + r * S::NGJ + c;
-      cp_async4(d + 0 * S::NG, a.seeds + S_GXX * plane + o, ok);
-      cp_async4(d + 1 * S::NG, a.seeds + S_GYX * plane + o, ok);
-      cp_async4(d + 2 * S::NG, a.seeds + S_GXY * plane + o, ok);
-      cp_async4(d + 3 * S::NG, a.seeds + S_GYY * plane + o, ok);
+      cp_async4(d + 0 * S::NG, rg.seeds + S_GXX * plane + o, ok);
+      cp_async4(d + 1 * S::NG, rg.seeds + S_GYX * plane + o, ok);
+      cp_async4(d + 2 * S::NG, rg.seeds + S_GXY * plane + o, ok);
+      cp_async4(d + 3 * S::NG, rg.seeds + S_GYY * plane + o, ok);
     }
   }
   cp_async_wait_all();
@@ -252,9 +253,23 @@ __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ B
       float acc = 0.f;
       for (int x = ra0; x <= ra1; ++x)
         for (int y = rb0; y <= rb1; ++y) acc += sdc[x * S::GB_MAX + y];
-      a.dJdC[(size_t)ga * g.my + gb] = acc;
+      rg.dJdC[(size_t)ga * g.my + gb] = acc;
     }
   }
+}
+
+template <int RP1, int BC>
+__global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ BwdArgs a) {
+  bwd_tile<RP1, BC>(a, a.r, blockIdx.y * TA, blockIdx.x * TB);
+}
+
+template <int RP1, int BC>
+__global__ void __launch_bounds__(NTHREADS) bwd_batched_kernel(const __grid_constant__ BwdBatchArgs a) {
+  int k, t;
+  batch_tile(a, blockIdx.x, k, t);
+  const int tj = a.tiles_j[k];
+  const int ti = t / tj;
+  bwd_tile<RP1, BC>(a, a.r[k], ti * TA, (t - ti * tj) * TB);
 }
 
 }  // namespace epsc

@@ -54,7 +54,8 @@ struct Geometry {
   float beta, eta, eps_core, eps_clad, deps;
 };
 
-struct FwdArgs {
+// One design region as seen by the stencil kernel.
+struct FwdRegion {
   Geometry g;
   int mode;
   int write_eps;
@@ -64,22 +65,59 @@ struct FwdArgs {
   float *eps;
   float *offdiag;
   const float *W;                // [4][nx][ny] Eq. 1 column sums (contraction kernel)
-  float *seeds;
+  float *seeds;                  // [NSEED][nx][ny]
   float *pd4;                    // [mx][my] P'(u) (eps_core - eps_clad) / 4
   float *ie2;                    // [mx][my] 1 / eps^2
+};
+
+struct FwdArgs {
+  FwdRegion r;
   int *err;
   float w[MAX_BOX * MAX_BOX];    // conic weights, dense (2 RP1 - 1)^2 box, row-major
 };
 
-struct BwdArgs {
+// Batched stencil launch: regions sharing one conic filter; block b works on
+// tile b - tile_start[k] of region k, tile_start[k] <= b < tile_start[k+1].
+struct FwdBatchArgs {
+  int n;
+  int tile_start[EPS_MAX_BATCH + 1];
+  int tiles_j[EPS_MAX_BATCH];
+  FwdRegion r[EPS_MAX_BATCH];
+  int *err;
+  float w[MAX_BOX * MAX_BOX];
+};
+
+// One design region as seen by the adjoint scatter kernel.
+struct BwdRegion {
   Geometry g;
   const float *seeds;
   const float *pd4;
   const float *ie2;
   float *dJdC;
+};
+
+struct BwdArgs {
+  BwdRegion r;
   int *err;
   float w[MAX_BOX * MAX_BOX];
 };
+
+struct BwdBatchArgs {
+  int n;
+  int tile_start[EPS_MAX_BATCH + 1];
+  int tiles_j[EPS_MAX_BATCH];
+  BwdRegion r[EPS_MAX_BATCH];
+  int *err;
+  float w[MAX_BOX * MAX_BOX];
+};
+
+// Region and tile of block b in a batched launch (regions scanned in order).
+template <class BA>
+__device__ __forceinline__ void batch_tile(const BA &a, int b, int &k, int &t) {
+  k = 0;
+  while (k + 1 < a.n && b >= a.tile_start[k + 1]) ++k;
+  t = b - a.tile_start[k];
+}
 
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return min(max(x, lo), hi); }
 

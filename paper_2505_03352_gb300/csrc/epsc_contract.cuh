@@ -173,4 +173,80 @@ __global__ void __launch_bounds__(NTHREADS) contract_kernel(const __grid_constan
   }
 }
 
+// ---- batched contraction: many regions in one launch -------------------
+
+struct ContractBatchRegion {
+  long col_start;                         // first column in the launch's column space
+  int nz, k0, nk, nlambda;
+  float *W;                               // [4][nx][ny] of this region
+  const float *EF[EPS_MAX_BATCH_LAMBDA];
+  const float *EA[EPS_MAX_BATCH_LAMBDA];
+  float fs[EPS_MAX_BATCH_LAMBDA][3];
+};
+
+struct ContractBatchArgs {
+  int n;
+  long ncol;                              // total columns over all regions
+  ContractBatchRegion r[EPS_MAX_BATCH];
+};
+
+// Eight lanes per column, 16-byte pieces (any even nz, 16-byte aligned
+// fields); the columns of all regions form one index space.
+template <int V>
+__global__ void __launch_bounds__(NTHREADS) contract_batched_kernel(const __grid_constant__ ContractBatchArgs a) {
+  constexpr int L = 8, GPW = 32 / L;
+  griddep_launch_dependents();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gl = lane & (L - 1), gw = lane / L;
+  const long step = (long)gridDim.x * (NTHREADS / 32) * GPW;
+  for (long wbase = ((long)blockIdx.x * (NTHREADS / 32) + warp) * GPW; wbase < a.ncol; wbase += step) {
+    const long col = wbase + gw;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int k = 0;
+    if (col < a.ncol) {
+      while (k + 1 < a.n && col >= a.r[k + 1].col_start) ++k;
+      const ContractBatchRegion &rg = a.r[k];
+      const long lc = col - rg.col_start;
+      const long ncr = (k + 1 < a.n ? a.r[k + 1].col_start : a.ncol) - rg.col_start;
+      const size_t cstride = (size_t)ncr * rg.nz * 2;
+      const int klo = rg.k0, khi = rg.k0 + rg.nk;
+      for (int l = 0; l < rg.nlambda; ++l) {
+        const float *ef = rg.EF[l];
+        const float *ea = rg.EA[l];
+        for (int pc = (klo >> 1) + gl; pc <= (khi >> 1); pc += L) {
+          const size_t off = (size_t)lc * rg.nz * 2 + (size_t)pc * 4;
+          float re0[3], re1[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float4 f = ld_piece(ef + c * cstride + off);
+            const float4 e = ld_piece(ea + c * cstride + off);
+            re0[c] = fmaf(f.x, e.x, -f.y * e.y);
+            re1[c] = fmaf(f.z, e.z, -f.w * e.w);
+          }
+          const int kk = 2 * pc;
+          const bool xy0 = kk >= klo + 1 && kk <= khi, xy1 = kk + 1 >= klo + 1 && kk + 1 <= khi;
+          const bool zi0 = kk >= klo + 1 && kk <= khi - 1, zi1 = kk + 1 >= klo + 1 && kk + 1 <= khi - 1;
+          const bool zf0 = kk == klo || kk == khi, zf1 = kk + 1 == klo || kk + 1 == khi;
+          acc[0] = fmaf(rg.fs[l][0], (xy0 ? re0[0] : 0.f) + (xy1 ? re1[0] : 0.f), acc[0]);
+          acc[1] = fmaf(rg.fs[l][1], (xy0 ? re0[1] : 0.f) + (xy1 ? re1[1] : 0.f), acc[1]);
+          acc[2] = fmaf(rg.fs[l][2], (zi0 ? re0[2] : 0.f) + (zi1 ? re1[2] : 0.f), acc[2]);
+          acc[3] = fmaf(rg.fs[l][2], (zf0 ? re0[2] : 0.f) + (zf1 ? re1[2] : 0.f), acc[3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int off = L / 2; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+    }
+    if (gl == 0 && col < a.ncol) {
+      const ContractBatchRegion &rg = a.r[k];
+      const long lc = col - rg.col_start;
+      const long ncr = (k + 1 < a.n ? a.r[k + 1].col_start : a.ncol) - rg.col_start;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rg.W[(size_t)q * ncr + lc] = acc[q];
+    }
+  }
+}
+
 }  // namespace epsc

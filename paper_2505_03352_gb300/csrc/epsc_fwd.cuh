@@ -57,8 +57,11 @@ __device__ __forceinline__ int bc_map_t(int x, int n) {
   return BC == EPS_BC_CLAMP ? clampi(x, 0, n - 1) : wrapi(x, n);
 }
 
-template <int RP1, int BC>
-__global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant__ FwdArgs a) {
+// One tile (rows i0 .., columns j0 ..) of one region `rg`; `a` supplies the
+// conic weights as compile-time-indexed kernel parameters.
+template <int RP1, int BC, class Args>
+__device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, const int i0,
+                                         const int j0) {
   using S = FwdSmem<RP1>;
   constexpr int R = S::R;
   constexpr int CB = S::CB;
@@ -70,10 +73,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
   float *sUx = smem + S::OFF_UX;
   float *sUy = smem + S::OFF_UY;
 
-  const Geometry &g = a.g;
+  const Geometry &g = rg.g;
   const int tid = threadIdx.x;
-  const int j0 = blockIdx.x * TJ;
-  const int i0 = blockIdx.y * TI;
   const int ua0 = 2 * i0 - 3;
   const int ub0 = 2 * j0 - 3;
   const int ca0 = ua0 - R;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
     const int c = idx - r * CB;
     const int ga = bc_map_t<BC>(ca0 + r, g.mx);
     const int gb = bc_map_t<BC>(cb0 + c, g.my);
-    cp_async4(sC + idx, a.C + (size_t)ga * g.my + gb, true);
+    cp_async4(sC + idx, rg.C + (size_t)ga * g.my + gb, true);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
   // with 1 - rho = exp(-2x) rho, and 1/eps^2 of the core subpixels go to the
   // workspace for the scatter kernel.
   constexpr int NSTRIP = UA / NA_F;
-  const bool vjp = a.mode != MODE_FWD;
+  const bool vjp = rg.mode != MODE_FWD;
   for (int item = tid; item < NSTRIP * UB; item += NTHREADS) {
     const int s = item / UB;
     const int col = item - s * UB;
@@ -124,8 +125,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
         const int ra = r0 + k - 3, rb = col - 3;   // core subpixel of the tile?
         if (ra >= 0 && ra < 2 * nvi && rb >= 0 && rb < 2 * nvj) {
           const size_t go = (size_t)(2 * i0 + ra) * g.my + 2 * j0 + rb;
-          a.pd4[go] = 0.5f * g.beta * g.deps * (ex2 * rho * rho);
-          a.ie2[go] = ie * ie;
+          rg.pd4[go] = 0.5f * g.beta * g.deps * (ex2 * rho * rho);
+          rg.ie2[go] = ie * ie;
         }
       }
     }
@@ -224,12 +225,12 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
   // rounds (waiting for the previous round's copies to read shared memory),
   // and plane counts that are not a multiple of 4 use direct stores.
   bool bulk_pending = false;
-  if (a.write_eps || a.write_offdiag) {
-    const int c_first = a.write_eps ? 0 : 3;
-    const int c_last = a.write_offdiag ? 4 : 2;
+  if (rg.write_eps || rg.write_offdiag) {
+    const int c_first = rg.write_eps ? 0 : 3;
+    const int c_last = rg.write_offdiag ? 4 : 2;
     const size_t cplane = (size_t)g.nx * g.ny * g.nz;
     const int comp_floats = TI * TJ * g.nz;
-    const int per_round = a.stage_floats / comp_floats;
+    const int per_round = rg.stage_floats / comp_floats;
     if ((g.nz & 3) == 0 && per_round >= 1) {
       float *sbuf = smem;   // the stencil buffers are dead from here on
       const int nz4 = g.nz >> 2;
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
         __syncthreads();
         if (tid == 0) {
           for (int comp = c0; comp <= c1; ++comp) {
-            float *base = comp < 3 ? a.eps + comp * cplane : a.offdiag + (comp - 3) * cplane;
+            float *base = comp < 3 ? rg.eps + comp * cplane : rg.offdiag + (comp - 3) * cplane;
             for (int r = 0; r < nvi; ++r)
               bulk_store(base + ((size_t)(i0 + r) * g.ny + j0) * g.nz,
                          sbuf + (comp - c0) * comp_floats + r * TJ * g.nz,
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
     } else if (valid) {
       // plane counts not a multiple of 4: thread per column
       for (int comp = c_first; comp <= c_last; ++comp) {
-        float *base = comp < 3 ? a.eps + comp * cplane : a.offdiag + (comp - 3) * cplane;
+        float *base = comp < 3 ? rg.eps + comp * cplane : rg.offdiag + (comp - 3) * cplane;
         const float vm = comp == 0 ? ex : comp == 1 ? ey : comp == 3 ? odx : ody;
         float *dst = base + ((size_t)ci * g.ny + cj) * g.nz;
         for (int k = 0; k < g.nz; ++k)
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
       }
     }
   }
-  if (a.mode == MODE_FWD) {
+  if (rg.mode == MODE_FWD) {
     if (bulk_pending && tid == 0) bulk_wait_all();
     return;
   }
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
   // ---- 6. adjoint seeds -------------------------------------------------
   if (valid) {
     const size_t plane = (size_t)g.nx * g.ny;
-    const float *wc = a.W + (size_t)ci * g.ny + cj;
+    const float *wc = rg.W + (size_t)ci * g.ny + cj;
     const float Wx = wc[0 * plane], Wy = wc[1 * plane];
     const float Wzi = wc[2 * plane], Wzf = wc[3 * plane];
     // eps = 1/(m H + (1-m)/A):  de/dH = -eps^2 m, de/dA = eps^2 (1-m)/A^2, de/dm = -eps^2 (H - 1/A)
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
     }
     const float dAz = Wzi;
     const float dHz = -0.5f * ezf * ezf * Wzf;
-    float *sd = a.seeds + (size_t)ci * g.ny + cj;
+    float *sd = rg.seeds + (size_t)ci * g.ny + cj;
     sd[S_DAX * plane] = dAx;
     sd[S_DHX * plane] = dHx;
     sd[S_GXX * plane] = dgxx;
@@ -333,6 +334,20 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant_
     sd[S_DHZ * plane] = dHz;
   }
   if (bulk_pending && tid == 0) bulk_wait_all();
+}
+
+template <int RP1, int BC>
+__global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant__ FwdArgs a) {
+  fwd_tile<RP1, BC>(a, a.r, blockIdx.y * TI, blockIdx.x * TJ);
+}
+
+template <int RP1, int BC>
+__global__ void __launch_bounds__(NTHREADS, 3) fwd_batched_kernel(const __grid_constant__ FwdBatchArgs a) {
+  int k, t;
+  batch_tile(a, blockIdx.x, k, t);
+  const int tj = a.tiles_j[k];
+  const int ti = t / tj;
+  fwd_tile<RP1, BC>(a, a.r[k], ti * TI, (t - ti * tj) * TJ);
 }
 
 }  // namespace epsc

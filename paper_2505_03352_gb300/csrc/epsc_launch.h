@@ -14,13 +14,15 @@ struct KernelEntry {
 
 // Defined in the instantiation units (RP1 1..6 in *_a, 7..12 in *_b);
 // return {nullptr, 0} outside their range.
-KernelEntry fwd_entry_a(int rp1, int bc);
-KernelEntry fwd_entry_b(int rp1, int bc);
-KernelEntry bwd_entry_a(int rp1, int bc);
-KernelEntry bwd_entry_b(int rp1, int bc);
+KernelEntry fwd_entry_a(int rp1, int bc, bool batched);
+KernelEntry fwd_entry_b(int rp1, int bc, bool batched);
+KernelEntry bwd_entry_a(int rp1, int bc, bool batched);
+KernelEntry bwd_entry_b(int rp1, int bc, bool batched);
 
 // Contraction kernel with 4 or 8 lanes per column.
 const void *contract_entry(int lanes);
+// Contraction over many regions in one launch.
+const void *contract_batched_entry();
 // Contraction kernel fed by bulk tensor copies (complex64 fields).
 const void *contract_tma_entry();
 
@@ -30,11 +32,11 @@ const void *pack_entry();
 const void *pack_finish_entry();
 const void *contract_packed_entry();
 
-inline KernelEntry fwd_entry(int rp1, int bc) {
-  return rp1 <= 6 ? fwd_entry_a(rp1, bc) : fwd_entry_b(rp1, bc);
+inline KernelEntry fwd_entry(int rp1, int bc, bool batched = false) {
+  return rp1 <= 6 ? fwd_entry_a(rp1, bc, batched) : fwd_entry_b(rp1, bc, batched);
 }
-inline KernelEntry bwd_entry(int rp1, int bc) {
-  return rp1 <= 6 ? bwd_entry_a(rp1, bc) : bwd_entry_b(rp1, bc);
+inline KernelEntry bwd_entry(int rp1, int bc, bool batched = false) {
+  return rp1 <= 6 ? bwd_entry_a(rp1, bc, batched) : bwd_entry_b(rp1, bc, batched);
 }
 
 }  // namespace epsc

@@ -1,18 +1,37 @@
-// Explicit instantiations of the forward kernel for RP1 = 1 .. 6, both boundary rules.
+// Explicit instantiations of the forward (stencil) kernels for RP1 = 1 .. 6, both
+// boundary rules, single-region and batched.
 #include "epsc_fwd.cuh"
 #include "epsc_launch.h"
 
 namespace epsc {
 
-KernelEntry fwd_entry_a(int rp1, int bc) {
+KernelEntry fwd_entry_a(int rp1, int bc, bool batched) {
   const bool clamp = bc == EPS_BC_CLAMP;
   switch (rp1) {
-    case 1: return {clamp ? (const void *)&fwd_kernel<1, EPS_BC_CLAMP> : (const void *)&fwd_kernel<1, EPS_BC_PERIODIC>, FwdSmem<1>::BYTES};
-    case 2: return {clamp ? (const void *)&fwd_kernel<2, EPS_BC_CLAMP> : (const void *)&fwd_kernel<2, EPS_BC_PERIODIC>, FwdSmem<2>::BYTES};
-    case 3: return {clamp ? (const void *)&fwd_kernel<3, EPS_BC_CLAMP> : (const void *)&fwd_kernel<3, EPS_BC_PERIODIC>, FwdSmem<3>::BYTES};
-    case 4: return {clamp ? (const void *)&fwd_kernel<4, EPS_BC_CLAMP> : (const void *)&fwd_kernel<4, EPS_BC_PERIODIC>, FwdSmem<4>::BYTES};
-    case 5: return {clamp ? (const void *)&fwd_kernel<5, EPS_BC_CLAMP> : (const void *)&fwd_kernel<5, EPS_BC_PERIODIC>, FwdSmem<5>::BYTES};
-    case 6: return {clamp ? (const void *)&fwd_kernel<6, EPS_BC_CLAMP> : (const void *)&fwd_kernel<6, EPS_BC_PERIODIC>, FwdSmem<6>::BYTES};
+    case 1:
+      if (batched)
+        return {clamp ? (const void *)&fwd_batched_kernel<1, EPS_BC_CLAMP> : (const void *)&fwd_batched_kernel<1, EPS_BC_PERIODIC>, FwdSmem<1>::BYTES};
+      return {clamp ? (const void *)&fwd_kernel<1, EPS_BC_CLAMP> : (const void *)&fwd_kernel<1, EPS_BC_PERIODIC>, FwdSmem<1>::BYTES};
+    case 2:
+      if (batched)
+        return {clamp ? (const void *)&fwd_batched_kernel<2, EPS_BC_CLAMP> : (const void *)&fwd_batched_kernel<2, EPS_BC_PERIODIC>, FwdSmem<2>::BYTES};
+      return {clamp ? (const void *)&fwd_kernel<2, EPS_BC_CLAMP> : (const void *)&fwd_kernel<2, EPS_BC_PERIODIC>, FwdSmem<2>::BYTES};
+    case 3:
+      if (batched)
+        return {clamp ? (const void *)&fwd_batched_kernel<3, EPS_BC_CLAMP> : (const void *)&fwd_batched_kernel<3, EPS_BC_PERIODIC>, FwdSmem<3>::BYTES};
+      return {clamp ? (const void *)&fwd_kernel<3, EPS_BC_CLAMP> : (const void *)&fwd_kernel<3, EPS_BC_PERIODIC>, FwdSmem<3>::BYTES};
+    case 4:
+      if (batched)
+        return {clamp ? (const void *)&fwd_batched_kernel<4, EPS_BC_CLAMP> : (const void *)&fwd_batched_kernel<4, EPS_BC_PERIODIC>, FwdSmem<4>::BYTES};
+      return {clamp ? (const void *)&fwd_kernel<4, EPS_BC_CLAMP> : (const void *)&fwd_kernel<4, EPS_BC_PERIODIC>, FwdSmem<4>::BYTES};
+    case 5:
+      if (batched)
+        return {clamp ? (const void *)&fwd_batched_kernel<5, EPS_BC_CLAMP> : (const void *)&fwd_batched_kernel<5, EPS_BC_PERIODIC>, FwdSmem<5>::BYTES};
+      return {clamp ? (const void *)&fwd_kernel<5, EPS_BC_CLAMP> : (const void *)&fwd_kernel<5, EPS_BC_PERIODIC>, FwdSmem<5>::BYTES};
+    case 6:
+      if (batched)
+        return {clamp ? (const void *)&fwd_batched_kernel<6, EPS_BC_CLAMP> : (const void *)&fwd_batched_kernel<6, EPS_BC_PERIODIC>, FwdSmem<6>::BYTES};
+      return {clamp ? (const void *)&fwd_kernel<6, EPS_BC_CLAMP> : (const void *)&fwd_kernel<6, EPS_BC_PERIODIC>, FwdSmem<6>::BYTES};
     default: return {nullptr, 0};
   }
 }

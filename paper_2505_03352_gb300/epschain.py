@@ -98,6 +98,13 @@ _PROTOS = {
     "eps_vjp_real": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP,
                                     ctypes.c_size_t, _VP]),
     "eps_sync_status": (ctypes.c_int, [_VP]),
+    "eps_batched_workspace_size": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(eps_problem_t),
+                                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "eps_forward_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(eps_problem_t), _VP, _VP,
+                                           _VP]),
+    "eps_vjp_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(eps_problem_t), _VP,
+                                       ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_float,
+                                       _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "eps_packed_field_bytes": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_size_t)]),
     "eps_field_pack": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), ctypes.c_int32, _VP, _VP,
@@ -287,6 +294,75 @@ def eps_field_pack(prob: Problem, field_type: int, E, out=None, stream=None):
     _check(lib().eps_field_pack(ctypes.byref(p), field_type, _ptr(E), _ptr(out), out.numel(),
                                 _stream(stream)), "eps_field_pack")
     return out
+
+
+def _probs(probs):
+    arr = (eps_problem_t * max(len(probs), 1))()
+    for k, p in enumerate(probs):
+        arr[k] = p.c_struct()
+    return arr
+
+
+def _ptrs(ts):
+    return (ctypes.c_void_p * max(len(ts), 1))(*[None if t is None else t.data_ptr() for t in ts])
+
+
+def eps_batched_workspace_size(probs, n_lambda: int = 1) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().eps_batched_workspace_size(len(probs), _probs(probs), n_lambda, ctypes.byref(n)),
+           "eps_batched_workspace_size")
+    return n.value
+
+
+def eps_forward_batched(probs, Cs, eps=None, stream=None):
+    """eps_hat of every region in one call; returns the list of eps tensors."""
+    import torch
+    if eps is None:
+        eps = [torch.empty((3, p.nx, p.ny, p.nz), dtype=torch.float32, device=C.device)
+               for p, C in zip(probs, Cs)]
+    for p, C, e in zip(probs, Cs, eps):
+        _need(C, (p.mx, p.my), torch.float32, "C")
+        _need(e, (3, p.nx, p.ny, p.nz), torch.float32, "eps")
+    _check(lib().eps_forward_batched(len(probs), _probs(probs), _ptrs(Cs), _ptrs(eps),
+                                     _stream(stream)), "eps_forward_batched")
+    return eps
+
+
+class BatchedVjp:
+    """eps_vjp_batched over a fixed set of regions with its arguments built
+    once (and its workspace and outputs allocated once), so that the call can
+    be repeated or captured in a CUDA graph.  EF[k] / EA[k] are lists of
+    complex64 fields of region k (one per wavelength)."""
+
+    def __init__(self, probs, Cs, EF, EA, scale=-2.0, with_eps=True, ws=None):
+        import torch
+        n = len(probs)
+        nl = len(EF[0]) if n else 0
+        dev = Cs[0].device
+        for k, p in enumerate(probs):
+            _need(Cs[k], (p.mx, p.my), torch.float32, f"C[{k}]")
+            for l in range(nl):
+                _need(EF[k][l], (3, p.nx, p.ny, p.nz), torch.complex64, f"EF[{k}][{l}]")
+                _need(EA[k][l], (3, p.nx, p.ny, p.nz), torch.complex64, f"EA[{k}][{l}]")
+        self.dJdC = [torch.empty((p.mx, p.my), dtype=torch.float32, device=dev) for p in probs]
+        self.eps = ([torch.empty((3, p.nx, p.ny, p.nz), dtype=torch.float32, device=dev)
+                     for p in probs] if with_eps else None)
+        need = eps_batched_workspace_size(probs, nl)
+        self.ws = ws if ws is not None else torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        self._keep = (Cs, EF, EA)
+        self._p = _probs(probs)
+        self._C = _ptrs(Cs)
+        self._EF = _ptrs([t for k in range(n) for t in EF[k]])
+        self._EA = _ptrs([t for k in range(n) for t in EA[k]])
+        self._G = _ptrs(self.dJdC)
+        self._E = _ptrs(self.eps) if with_eps else None
+        self._args = (n, self._p, self._C, nl, EPS_FIELD_C64, self._EF, self._EA, None,
+                      float(scale), self._G, self._E, _ptr(self.ws), self.ws.numel())
+        self._fn = lib().eps_vjp_batched
+
+    def __call__(self, stream=None):
+        _check(self._fn(*self._args, _stream(stream)), "eps_vjp_batched")
+        return self.dJdC, self.eps
 
 
 def eps_sync_status(stream=None):

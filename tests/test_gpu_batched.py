@@ -1,0 +1,107 @@
+"""Batched calls: many regions of uneven size, radius, beta and boundary
+rule in one call, against the per-region calls and the FP64 oracle; and the
+batched call captured in a CUDA graph."""
+
+import numpy as np
+import pytest
+
+from oracle import epschain_oracle as orc
+from paper_2505_03352_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def region_set(n=14, seed=21):
+    rng = np.random.default_rng(seed)
+    regs = []
+    for r in range(n):
+        side_a = int(rng.integers(8, 90)) * 2
+        side_b = int(rng.integers(8, 90)) * 2
+        regs.append(dict(mx=side_a, my=side_b, nz=int(rng.choice([16, 24])),
+                         radius=float(rng.integers(2, 9)), beta=float(rng.choice([4, 8, 16, 32])),
+                         bc=int(rng.integers(0, 2)), seed=1000 + r))
+    return regs
+
+
+def inputs(regs):
+    import torch
+
+    import paper_2505_03352_gb300 as ec
+    probs, Cs, EF, EA, raw = [], [], [], [], []
+    for d in regs:
+        p = ec.Problem(mx=d["mx"], my=d["my"], nz=d["nz"], radius=d["radius"], beta=d["beta"],
+                       bc=d["bc"])
+        C = synth.soi_layout(d["mx"], d["my"], d["seed"])
+        ef = synth.complex_field((3, p.nx, p.ny, p.nz), d["seed"] + 1)
+        ea = synth.complex_field((3, p.nx, p.ny, p.nz), d["seed"] + 2)
+        probs.append(p)
+        Cs.append(torch.from_numpy(C).cuda())
+        EF.append([torch.from_numpy(ef).cuda()])
+        EA.append([torch.from_numpy(ea).cuda()])
+        raw.append((C, ef, ea))
+    return probs, Cs, EF, EA, raw
+
+
+def test_batched_equals_per_region_and_oracle():
+    import paper_2505_03352_gb300 as ec
+    regs = region_set()
+    probs, Cs, EF, EA, raw = inputs(regs)
+    bv = ec.BatchedVjp(probs, Cs, EF, EA)
+    G, E = bv()
+    ec.eps_sync_status()
+    for k, p in enumerate(probs):
+        g1, e1 = ec.eps_vjp(p, Cs[k], EF[k], EA[k], eps_out=True)
+        ec.eps_sync_status()
+        g1, e1 = g1.cpu().numpy(), e1.cpu().numpy()
+        gb, eb = G[k].cpu().numpy(), E[k].cpu().numpy()
+        np.testing.assert_array_equal(eb, e1)   # same stencil code per tile
+        assert np.max(np.abs(gb - g1)) <= 1e-5 * np.max(np.abs(g1))
+        C, ef, ea = raw[k]
+        o = orc.Problem(mx=p.mx, my=p.my, nz=p.nz, radius=p.radius, beta=p.beta, bc=p.bc)
+        ref = orc.vjp_fields(o, C, [ef], [ea])
+        assert np.max(np.abs(gb - ref)) / np.max(np.abs(ref)) <= 1e-4
+        assert np.max(np.abs(eb - orc.eps_hat(o, C)) / orc.eps_hat(o, C)) <= 1e-5
+
+
+def test_forward_batched_equals_per_region():
+    import paper_2505_03352_gb300 as ec
+    regs = region_set(9, seed=5)
+    probs, Cs, _, _, _ = inputs(regs)
+    E = ec.eps_forward_batched(probs, Cs)
+    ec.eps_sync_status()
+    for k, p in enumerate(probs):
+        e1 = ec.eps_forward(p, Cs[k])
+        ec.eps_sync_status()
+        np.testing.assert_array_equal(E[k].cpu().numpy(), e1.cpu().numpy())
+
+
+def test_batched_call_in_a_cuda_graph():
+    import torch
+
+    import paper_2505_03352_gb300 as ec
+    regs = region_set(10, seed=8)
+    probs, Cs, EF, EA, _ = inputs(regs)
+    bv = ec.BatchedVjp(probs, Cs, EF, EA)
+    G0, E0 = bv()
+    torch.cuda.synchronize()
+    ref = [g.clone() for g in G0]
+    refe = [e.clone() for e in E0]
+    for g in G0:
+        g.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bv(stream=s)          # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bv()
+    for g in G0:
+        g.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    ec.eps_sync_status()
+    for k in range(len(probs)):
+        torch.testing.assert_close(G0[k], ref[k], rtol=0, atol=0)
+        torch.testing.assert_close(E0[k], refe[k], rtol=0, atol=0)
