@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the cfg3 / batched cfg4 / reduced-precision cfg5 measurements")
     return ap.parse_args()
 
 
@@ -360,6 +362,9 @@ def run_ours(args, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
+    variants = None
+    if rank == 0 and world == 1 and not args.no_variants:
+        variants = run_variants(torch, ec, synth, dev, flush_l2)
 
     if rank == 0:
         line = {
@@ -375,6 +380,7 @@ def run_ours(args, rank, world, local):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * K)),
+            "variants": variants,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -382,6 +388,145 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.destroy_process_group()
     del np
+
+
+# ------------------------------------------------------------------ variants
+
+def _timed(call, flush_l2, K, torch):
+    """Mean milliseconds of `call` over K steps, L2 flushed before each."""
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        flush_l2()
+        call()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(K):
+        flush_l2()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / K
+
+
+def _device_fields(torch, shape, n, seed, dev):
+    g = torch.Generator(device=dev)
+    out = []
+    for l in range(n):
+        g.manual_seed(seed + l)
+        out.append(torch.randn(tuple(shape) + (2,), generator=g, device=dev).view(torch.complex64)[..., 0]
+                   .contiguous())
+    return out
+
+
+def _window_error(w, C, EF, EA, g_gpu, half=48):
+    """max |dJ/dC - oracle| / max |oracle| on windows of the full problem."""
+    import numpy as np
+    from oracle import epschain_oracle as orc
+    margin = int(2 * np.ceil(w.radius)) + 8
+    worst = 0.0
+    for (ca, cb) in [(0, 0), (w.mx // 2, w.my // 2), (w.mx, w.my)]:
+        a0 = max(0, ca - half) // 2 * 2
+        b0 = max(0, cb - half) // 2 * 2
+        a1, b1 = min(w.mx, a0 + 2 * half), min(w.my, b0 + 2 * half)
+        wa0, wb0 = max(0, a0 - margin), max(0, b0 - margin)
+        wa1, wb1 = min(w.mx, a1 + margin), min(w.my, b1 + margin)
+        o = orc.Problem(mx=wa1 - wa0, my=wb1 - wb0, nz=w.nz, radius=w.radius, beta=w.beta)
+        sl = (slice(None), slice(wa0 // 2, wa1 // 2), slice(wb0 // 2, wb1 // 2), slice(None))
+        ref = orc.vjp_fields(o, C[wa0:wa1, wb0:wb1], [e[sl].cpu().numpy() for e in EF],
+                             [e[sl].cpu().numpy() for e in EA])
+        rg = ref[a0 - wa0:a1 - wa0, b0 - wb0:b1 - wb0]
+        gg = g_gpu[a0:a1, b0:b1]
+        worst = max(worst, float(np.max(np.abs(gg - rg)) / np.max(np.abs(rg))))
+    return worst
+
+
+def run_variants(torch, ec, synth, dev, flush_l2):
+    """The differentiation (cfg3), batching (cfg4) and precision (cfg5) forms,
+    each timed like the main workload (L2 flushed before every call)."""
+    out = {}
+    peak, _ = measured_peaks()
+
+    # cfg3: 2000 x 2000 controls, 1000 x 1000 x 32, three wavelengths
+    w = synth.WORKLOADS[3]
+    p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+    C = torch.from_numpy(synth.controls(w)).to(dev)
+    EF = _device_fields(torch, (3, w.nx, w.ny, w.nz), 3, 2030, dev)
+    EA = _device_fields(torch, (3, w.nx, w.ny, w.nz), 3, 3030, dev)
+    G = torch.empty((w.mx, w.my), device=dev)
+    E = torch.empty((3, w.nx, w.ny, w.nz), device=dev)
+    call = ec.PreparedVjp(p, C, EF, EA, G, eps_out=E)
+    ms = _timed(call, flush_l2, 20, torch)
+    alg = algorithmic_bytes(w, 3)
+    out["cfg3_fp32_3wavelengths"] = {"workload": w.name, "value": w.voxels / (ms * 1e-3),
+                                     "unit": UNIT, "ms_per_call": round(ms, 4),
+                                     "whole_call_hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4)}
+    del C, EF, EA, G, E, call
+
+    # cfg4: 64 regions of uneven size, radius and beta; batched vs per region
+    regs = synth.batched_regions()
+    probs, Cs, EFs, EAs = [], [], [], []
+    for r, rw in enumerate(regs):
+        probs.append(ec.Problem(mx=rw.mx, my=rw.my, nz=rw.nz, radius=rw.radius, beta=rw.beta))
+        Cs.append(torch.from_numpy(synth.soi_layout(rw.mx, rw.my, 1004 * 1000 + r)).to(dev))
+        EFs.append(_device_fields(torch, (3, rw.nx, rw.ny, rw.nz), 1, 2040 * 1000 + r, dev))
+        EAs.append(_device_fields(torch, (3, rw.nx, rw.ny, rw.nz), 1, 3040 * 1000 + r, dev))
+    vox = sum(rw.voxels for rw in regs)
+    bv = ec.BatchedVjp(probs, Cs, EFs, EAs)
+    bv()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bv()
+    ms_b = _timed(graph.replay, flush_l2, 20, torch)
+    singles = [ec.PreparedVjp(p, C, ef, ea, G, eps_out=E)
+               for p, C, ef, ea, G, E in zip(probs, Cs, EFs, EAs, bv.dJdC, bv.eps)]
+
+    def per_region():
+        for c in singles:
+            c()
+
+    ms_s = _timed(per_region, flush_l2, 20, torch)
+    out["cfg4_batched_64_regions"] = {
+        "regions": len(regs), "voxels": vox, "value": vox / (ms_b * 1e-3), "unit": UNIT,
+        "ms_per_call": round(ms_b, 4), "per_region_launches": {
+            "value": vox / (ms_s * 1e-3), "ms_per_call": round(ms_s, 4)},
+        "speedup_vs_per_region": round(ms_s / ms_b, 3),
+        "launch": "one CUDA graph: 1 contraction + 1 stencil and 1 scatter launch per radius group"}
+    del bv, graph, singles, Cs, EFs, EAs
+
+    # cfg5: 3000 x 3000, 1500 x 1500 x 32, eight wavelengths; FP32 / BF16 / FP16 fields
+    w = synth.WORKLOADS[5]
+    p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+    Ch = synth.controls(w)
+    C = torch.from_numpy(Ch).to(dev)
+    EF = _device_fields(torch, (3, w.nx, w.ny, w.nz), 8, 2050, dev)
+    EA = _device_fields(torch, (3, w.nx, w.ny, w.nz), 8, 3050, dev)
+    G = torch.empty((w.mx, w.my), device=dev)
+    E = torch.empty((3, w.nx, w.ny, w.nz), device=dev)
+    res = {}
+    call = ec.PreparedVjp(p, C, EF, EA, G, eps_out=E)
+    ms = _timed(call, flush_l2, 10, torch)
+    err = _window_error(w, Ch, EF, EA, G.cpu().numpy())
+    res["fp32"] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
+                   "algorithmic_bytes": algorithmic_bytes(w, 8),
+                   "dJdC_max_err_vs_fp64_oracle": err}
+    for name, ft in (("bf16", ec.EPS_FIELD_BF16X2_SCALED), ("fp16", ec.EPS_FIELD_F16X2_SCALED)):
+        PF = [ec.eps_field_pack(p, ft, e) for e in EF]
+        PA = [ec.eps_field_pack(p, ft, e) for e in EA]
+        call = ec.PreparedVjp(p, C, PF, PA, G, eps_out=E, field_type=ft)
+        ms = _timed(call, flush_l2, 10, torch)
+        err = _window_error(w, Ch, EF, EA, G.cpu().numpy())
+        alg = 8 * w.mx * w.my + 12 * w.nx * w.ny * w.nz + w.nx * w.ny * 8 * (3 * w.slab_nk + 1) * 2 * 4
+        res[name] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
+                     "algorithmic_bytes": alg, "dJdC_max_err_vs_fp64_oracle": err,
+                     "packed_bytes_per_field": ec.eps_packed_field_bytes(p, ft)}
+        del PF, PA, call
+    out["cfg5_precision_8wavelengths"] = dict(workload=w.name, unit=UNIT, **res)
+    return out
 
 
 # ------------------------------------------------------------ reference arm
