@@ -37,7 +37,7 @@ UNIT = "voxels/s"
 L2_FLUSH_BYTES = 256 << 20
 L2_FETCH_BYTES = 32
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SOURCES = ["paper_2505_03352_gb300/csrc/epsc_contract.cuh",
+KERNEL_SOURCES = ["paper_2505_03352_gb300/csrc/epsc_contract_tma.cuh",
                   "paper_2505_03352_gb300/csrc/epsc_common.cuh"]
 
 
