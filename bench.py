@@ -54,6 +54,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over the ranks of the default process group (x on
+    a single process)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank: float, world: int, steps: int, ms_total_max: float) -> float:
+    """Whole-job throughput: every rank processes its own units each step,
+    and the job takes as long as its slowest rank."""
+    return world * units_per_rank * steps / (ms_total_max * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -271,12 +289,7 @@ def run_ours(args, rank, world, local):
     t1 = time.time()
     barrier()
     ec.eps_sync_status()
-    ms_total = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
     time.sleep(0.25)
     clocks = None
     if sampler is not None:
@@ -284,7 +297,7 @@ def run_ours(args, rank, world, local):
         clocks = sampler.summary(t0, t1)
 
     ms_step = ms_total / K
-    value = world * w.voxels * K / (ms_total * 1e-3)
+    value = weak_scaling_value(w.voxels, world, K, ms_total)
 
     # per-kernel durations: the same steps again with the library's event
     # pairs around every launch (kernels then run without launch overlap)
@@ -348,13 +361,8 @@ def run_ours(args, rank, world, local):
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        e2e = {"value": world * w.voxels * args.e2e_steps / (ms * 1e-3), "unit": UNIT,
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": weak_scaling_value(w.voxels, world, args.e2e_steps, ms), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": round(ms / args.e2e_steps, 4),
                "path": "pinned host -> device copies, eps_vjp, device -> host copies, one stream"}
