@@ -252,9 +252,7 @@ eps_status_t run_contract(const ContractArgs &ca, int lanes, cudaStream_t s) {
   const long ncol = (long)ca.nx * ca.ny;
   const long per_block = (NTHREADS / lanes) * 2;   // columns per block per iteration
   long blocks = (ncol + per_block - 1) / per_block;
-  int bps = CONTRACT_BLOCKS_PER_SM;
-  if (const char *e = std::getenv("EPSC_EXP_CBPS")) bps = std::atoi(e);   // EXPERIMENT
-  blocks = std::min<long>(blocks, (long)nsm * bps);
+  blocks = std::min<long>(blocks, (long)nsm * CONTRACT_BLOCKS_PER_SM);
   return launch(ca.mode == MODE_C64 ? "eps_vjp_contract" : "eps_vjp_real_contract",
                 contract_entry(lanes), dim3((unsigned)std::max<long>(blocks, 1)), 0,
                 (void *)&ca, s);

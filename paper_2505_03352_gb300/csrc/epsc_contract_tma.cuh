@@ -23,7 +23,7 @@
 namespace epsc {
 
 constexpr int TMA_BY = 32;        // columns per box
-constexpr int TMA_NSTAGE = 4; // ring depth
+constexpr int TMA_NSTAGE = 2; // ring depth
 constexpr int TMA_BX_MAX = 64;    // floats per box row (support window)
 
 struct __align__(64) ContractTmaArgs {

@@ -249,16 +249,30 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
             const int kf0 = comp == 2 ? g.k0 : -8, kf1 = comp == 2 ? g.k0 + g.nk : -8;
             float4 *dst = reinterpret_cast<float4 *>(sbuf + (comp - c0) * comp_floats +
                                                      (cr * TJ + cc) * g.nz);
+            // The plane pattern is the same for every column, so each group
+            // of four planes is classified once (warp-uniform): all inside
+            // the value run, all outside it, or mixed (per-plane selects).
+            const int lo = g.k0 + 1, hi = g.k0 + zlen;       // value run [lo, hi]
+            const int flo = comp == 2 ? g.k0 : lo, fhi = comp == 2 ? g.k0 + g.nk : hi;
+            const float4 vin4 = make_float4(vin, vin, vin, vin);
+            const float4 out4 = make_float4(out, out, out, out);
             for (int k4 = 0; k4 < nz4; ++k4) {
-              float t[4];
+              const int k = 4 * k4;
+              if (k >= lo && k + 3 <= hi) {
+                dst[k4] = vin4;
+              } else if (k + 3 < flo || k > fhi) {
+                dst[k4] = out4;
+              } else {
+                float t[4];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const int k = 4 * k4 + q;
-                const bool in = (unsigned)(k - (g.k0 + 1)) < (unsigned)zlen;
-                const bool face = k == kf0 || k == kf1;
-                t[q] = in ? vin : (face ? ezf : out);
+                for (int q = 0; q < 4; ++q) {
+                  const int kk = k + q;
+                  const bool in = kk >= lo && kk <= hi;
+                  const bool face = kk == kf0 || kk == kf1;
+                  t[q] = in ? vin : (face ? ezf : out);
+                }
+                dst[k4] = make_float4(t[0], t[1], t[2], t[3]);
               }
-              dst[k4] = make_float4(t[0], t[1], t[2], t[3]);
             }
           }
         }
