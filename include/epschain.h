@@ -198,6 +198,54 @@ eps_status_t eps_field_pack(const eps_problem_t *prob, int32_t field_type, const
                             void *dst, size_t dst_bytes, eps_stream_t stream);
 
 /*
+ * Morphological filtering (Sec. 3, Eq. 3-6).  The chain becomes
+ *   u = K * C (Eq. 2),  rho_0 = (1 + tanh(beta (u - eta))) / 2 (Eq. 3),
+ *   rho_{k+1} = op_k(rho_k) for the listed operations, with the normalised
+ *     disk K_m (integer subpixel offsets with p^2 + q^2 <= radius^2, each
+ *     weight 1/count) and the prob's boundary rule:
+ *       dilate (Eq. 4):  (1/alpha) log sum_d K_m(d) exp(alpha rho[x+d])
+ *       erode  (Eq. 5):  1 - (1/alpha) log sum_d K_m(d) exp(alpha (1 - rho[x+d]))
+ *   then the final projection at 1/2 (Eq. 6) and the rest of the chain, with
+ *   the Sobel normals taken from rho_tilde = rho_n (the density whose 1/2
+ *   level set the final projection draws).  That is: the base chain of
+ *   eps_forward applied to rho_n with an identity filter and eta = 1/2.
+ *   alpha   (0, EPS_MORPH_MAX_ALPHA]; App. B uses 20
+ *   radius  disk radius d/2 in subpixels, 0 <= radius < EPS_MAX_RADIUS
+ *   n_ops   0 .. EPS_MORPH_MAX_OPS operations ops[0 .. n_ops-1], each an
+ *           eps_morph_op_t, applied in order (a closing then an opening is
+ *           DILATE, ERODE, ERODE, DILATE)
+ * The calls take a workspace of eps_morph_workspace_size() bytes (256-byte
+ * aligned); it holds the density maps rho_0 .. rho_n, P'(u), two adjoint
+ * maps and, after them, the base chain's workspace.  eps_vjp_morph and
+ * eps_vjp_real_morph have the arguments and results of eps_vjp /
+ * eps_vjp_real with dJ/dC taken through the whole chain.  Errors return
+ * before any launch.
+ */
+#define EPS_MORPH_MAX_OPS 8
+#define EPS_MORPH_MAX_ALPHA 60.0f
+typedef enum { EPS_MORPH_DILATE = 0, EPS_MORPH_ERODE = 1 } eps_morph_op_t;
+typedef struct {
+  float alpha;
+  float radius;
+  int32_t n_ops;
+  int32_t ops[EPS_MORPH_MAX_OPS];
+} eps_morph_t;
+
+eps_status_t eps_morph_workspace_size(const eps_problem_t *prob, const eps_morph_t *morph,
+                                      int32_t n_lambda, size_t *bytes);
+eps_status_t eps_forward_morph(const eps_problem_t *prob, const eps_morph_t *morph,
+                               const float *C, float *eps, float *offdiag, void *ws,
+                               size_t ws_bytes, eps_stream_t stream);
+eps_status_t eps_vjp_morph(const eps_problem_t *prob, const eps_morph_t *morph, const float *C,
+                           int32_t n_lambda, int32_t field_type, const void *const *EF,
+                           const void *const *EA, const float *field_scales, float scale,
+                           float *dJdC, float *eps_out, void *ws, size_t ws_bytes,
+                           eps_stream_t stream);
+eps_status_t eps_vjp_real_morph(const eps_problem_t *prob, const eps_morph_t *morph,
+                                const float *C, const float *G, float *dJdC, void *ws,
+                                size_t ws_bytes, eps_stream_t stream);
+
+/*
  * Synchronise `stream`, then return (and clear) any device-side error flag
  * raised by earlier calls on this device: EPS_ERR_DEVICE_TIMEOUT or
  * EPS_ERR_DEVICE_BOUNDS, else EPS_OK; EPS_ERR_CUDA if the sync failed.

@@ -12,7 +12,10 @@ from .epschain import (BatchedVjp, eps_batched_workspace_size, eps_forward_batch
                        eps_field_pack, eps_forward, eps_packed_field_bytes,
                        eps_profile_start, eps_profile_stop, eps_set_l2_fetch_granularity,
                        eps_status_string, eps_sync_status,
-                       eps_vjp, eps_vjp_real, eps_workspace_size, lib)
+                       eps_vjp, eps_vjp_real, eps_workspace_size, lib,
+                       CLOSE_THEN_OPEN, EPS_MORPH_DILATE, EPS_MORPH_ERODE, Morph,
+                       eps_forward_morph, eps_morph_workspace_size, eps_vjp_morph,
+                       eps_vjp_real_morph)
 
 __all__ = [
     "BatchedVjp", "eps_batched_workspace_size", "eps_forward_batched",
@@ -22,6 +25,8 @@ __all__ = [
     "eps_profile_start", "eps_profile_stop", "eps_set_l2_fetch_granularity", "eps_status_string",
     "eps_sync_status", "eps_vjp",
     "eps_vjp_real", "eps_workspace_size", "lib",
+    "CLOSE_THEN_OPEN", "EPS_MORPH_DILATE", "EPS_MORPH_ERODE", "Morph", "eps_forward_morph",
+    "eps_morph_workspace_size", "eps_vjp_morph", "eps_vjp_real_morph",
 ]
 
 from . import autograd  # noqa: E402  (torch.autograd wrappers)

@@ -15,7 +15,8 @@ from __future__ import annotations
 
 import torch
 
-from .epschain import EPS_FIELD_C64, Problem, eps_forward, eps_vjp, eps_vjp_real
+from .epschain import (EPS_FIELD_C64, Morph, Problem, eps_forward, eps_forward_morph, eps_vjp,
+                       eps_vjp_real, eps_vjp_real_morph)
 
 
 class EpsChain(torch.autograd.Function):
@@ -48,3 +49,30 @@ def adjoint_gradient(prob: Problem, C, EF, EA, scale: float = -2.0, field_type: 
     dJdC, eps = eps_vjp(prob, C, EF, EA, scale=scale, eps_out=True, field_type=field_type,
                         field_scales=field_scales, ws=ws, stream=stream)
     return eps, dJdC
+
+
+class EpsChainMorph(torch.autograd.Function):
+    """eps_hat(C) through the chain with morphological filtering (Eq. 3-6);
+    backward is eps_vjp_real_morph, which recomputes every map from C."""
+
+    @staticmethod
+    def forward(ctx, C, prob: Problem, morph: Morph):
+        if C.dtype != torch.float32:
+            raise TypeError("C must be float32")
+        C = C.contiguous()
+        eps = eps_forward_morph(prob, morph, C)
+        ctx.prob = prob
+        ctx.morph = morph
+        ctx.save_for_backward(C)
+        return eps
+
+    @staticmethod
+    def backward(ctx, grad_eps):
+        (C,) = ctx.saved_tensors
+        G = grad_eps.contiguous().to(torch.float32)
+        return eps_vjp_real_morph(ctx.prob, ctx.morph, C, G), None, None
+
+
+def eps_chain_morph(C, prob: Problem, morph: Morph):
+    """Differentiable eps_hat(C) with morphology (see EpsChainMorph)."""
+    return EpsChainMorph.apply(C, prob, morph)

@@ -438,19 +438,26 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps, 
   return launch("eps_forward", k.fn, fwd_grid(r.g), smem, &fa, (cudaStream_t)stream);
 }
 
-eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda,
-                     int32_t field_type, const void *const *EF, const void *const *EA,
-                     const float *field_scales, float scale, float *dJdC, float *eps_out,
-                     void *ws, size_t ws_bytes, eps_stream_t stream) {
-  Resolved r;
-  eps_status_t st = resolve(prob, &r);
-  if (st != EPS_OK) return st;
+}  // extern "C"
+
+namespace {
+
+// Argument checks of eps_vjp (everything but the problem itself, which
+// `r` already resolved); *skip is set for an empty problem.
+eps_status_t vjp_args(const Resolved &r, const float *C, int32_t n_lambda, int32_t field_type,
+                      const void *const *EF, const void *const *EA, const float *field_scales,
+                      float scale, const float *dJdC, const float *eps_out, const void *ws,
+                      size_t ws_bytes, bool *skip) {
+  *skip = false;
   if (n_lambda < 0 || n_lambda > EPS_MAX_LAMBDA) return EPS_ERR_INVALID_ARG;
   if (field_type != EPS_FIELD_C64 && field_type != EPS_FIELD_BF16X2_SCALED &&
       field_type != EPS_FIELD_F16X2_SCALED)
     return EPS_ERR_INVALID_ARG;
   if (!std::isfinite(scale)) return EPS_ERR_INVALID_ARG;
-  if (r.empty) return EPS_OK;
+  if (r.empty) {
+    *skip = true;
+    return EPS_OK;
+  }
   if (!C || !dJdC) return EPS_ERR_INVALID_ARG;
   if (n_lambda > 0 && (!EF || !EA)) return EPS_ERR_INVALID_ARG;
   for (int l = 0; l < n_lambda; ++l) {
@@ -464,6 +471,24 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   if (!aligned(C, 4) || !aligned(dJdC, 4) || (eps_out && !aligned(eps_out, 16)))
     return EPS_ERR_INVALID_ARG;
   if (!ws || !aligned(ws, 256) || ws_bytes < workspace_bytes(r.g)) return EPS_ERR_WORKSPACE;
+  return EPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda,
+                     int32_t field_type, const void *const *EF, const void *const *EA,
+                     const float *field_scales, float scale, float *dJdC, float *eps_out,
+                     void *ws, size_t ws_bytes, eps_stream_t stream) {
+  Resolved r;
+  eps_status_t st = resolve(prob, &r);
+  if (st != EPS_OK) return st;
+  bool skip = false;
+  st = vjp_args(r, C, n_lambda, field_type, EF, EA, field_scales, scale, dJdC, eps_out, ws,
+                ws_bytes, &skip);
+  if (st != EPS_OK || skip) return st;
   int *err = nullptr;
   if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
 
@@ -942,3 +967,35 @@ eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal host interface for the library's other translation units.
+namespace epsc_host {
+
+eps_status_t conic_filter(const eps_problem_t *prob, float *w, int *rp1) {
+  Resolved r;
+  const eps_status_t st = resolve(prob, &r);
+  if (st != EPS_OK) return st;
+  std::memcpy(w, r.w, sizeof(r.w));
+  *rp1 = r.rp1;
+  return EPS_OK;
+}
+
+eps_status_t check_vjp_args(const eps_problem_t *prob, const float *C, int32_t n_lambda,
+                            int32_t field_type, const void *const *EF, const void *const *EA,
+                            const float *field_scales, float scale, const float *dJdC,
+                            const float *eps_out, const void *ws, size_t ws_bytes) {
+  Resolved r;
+  eps_status_t st = resolve(prob, &r);
+  if (st != EPS_OK) return st;
+  bool skip = false;
+  return vjp_args(r, C, n_lambda, field_type, EF, EA, field_scales, scale, dJdC, eps_out, ws,
+                  ws_bytes, &skip);
+}
+
+eps_status_t launch_kernel(const char *name, const void *fn, dim3 grid, size_t smem, void *args,
+                           cudaStream_t s, bool pdl) {
+  return launch(name, fn, grid, smem, args, s, pdl);
+}
+
+}  // namespace epsc_host

@@ -1,0 +1,28 @@
+// Host-side helpers shared by the library's translation units (defined in
+// abi.cu).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "epschain.h"
+
+namespace epsc_host {
+
+// Validate `prob` as every entry point does and return the conic filter of
+// Eq. 2: weights in a dense (2 rp1 - 1)^2 box, row-major (w holds
+// MAX_BOX^2 floats), and rp1 = ceil(radius) (at least 1).
+eps_status_t conic_filter(const eps_problem_t *prob, float *w, int *rp1);
+
+// The argument checks eps_vjp makes before its first launch (an empty
+// problem passes).
+eps_status_t check_vjp_args(const eps_problem_t *prob, const float *C, int32_t n_lambda,
+                            int32_t field_type, const void *const *EF, const void *const *EA,
+                            const float *field_scales, float scale, const float *dJdC,
+                            const float *eps_out, const void *ws, size_t ws_bytes);
+
+// Launch one of the library's kernels (one by-value argument struct, 256
+// threads per block), with per-kernel timing while profiling is on.
+eps_status_t launch_kernel(const char *name, const void *fn, dim3 grid, size_t smem, void *args,
+                           cudaStream_t s, bool pdl);
+
+}  // namespace epsc_host

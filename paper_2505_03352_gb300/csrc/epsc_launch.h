@@ -32,6 +32,14 @@ const void *pack_entry();
 const void *pack_finish_entry();
 const void *contract_packed_entry();
 
+// Subpixel-map kernels of the morphology path (kind: MapKind).
+KernelEntry map_entry_a(int rp1, int bc, int kind);
+KernelEntry map_entry_b(int rp1, int bc, int kind);
+
+inline KernelEntry map_entry(int rp1, int bc, int kind) {
+  return rp1 <= 6 ? map_entry_a(rp1, bc, kind) : map_entry_b(rp1, bc, kind);
+}
+
 inline KernelEntry fwd_entry(int rp1, int bc, bool batched = false) {
   return rp1 <= 6 ? fwd_entry_a(rp1, bc, batched) : fwd_entry_b(rp1, bc, batched);
 }

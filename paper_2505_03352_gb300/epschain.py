@@ -113,6 +113,15 @@ _PROTOS = {
     "eps_set_l2_fetch_granularity": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "eps_profile_stop": (ctypes.c_int, [ctypes.POINTER(eps_profile_entry_t), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]),
+    "eps_morph_workspace_size": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+    "eps_forward_morph": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP,
+                                         ctypes.c_size_t, _VP]),
+    "eps_vjp_morph": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, ctypes.c_int32,
+                                     ctypes.c_int32, _VP, _VP, _VP, ctypes.c_float, _VP, _VP, _VP,
+                                     ctypes.c_size_t, _VP]),
+    "eps_vjp_real_morph": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP,
+                                          ctypes.c_size_t, _VP]),
 }
 
 
@@ -416,3 +425,125 @@ class PreparedVjp:
 
     def __call__(self, stream=None):
         _check(self._fn(*self._args, _stream(stream)), "eps_vjp")
+
+
+# --------------------------------------------------------------- morphology
+
+EPS_MORPH_DILATE, EPS_MORPH_ERODE = 0, 1
+EPS_MORPH_MAX_OPS = 8
+CLOSE_THEN_OPEN = (EPS_MORPH_DILATE, EPS_MORPH_ERODE, EPS_MORPH_ERODE, EPS_MORPH_DILATE)
+
+
+class eps_morph_t(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_float), ("radius", ctypes.c_float), ("n_ops", ctypes.c_int32),
+                ("ops", ctypes.c_int32 * EPS_MORPH_MAX_OPS)]
+
+
+@dataclass(frozen=True)
+class Morph:
+    """Soft dilate / erode sequence of Eq. 4/5: alpha (App. B: 20), disk
+    radius d/2 in subpixels, and the operations in order."""
+
+    alpha: float = 20.0
+    radius: float = 2.0
+    ops: tuple = CLOSE_THEN_OPEN
+
+    def c_struct(self) -> eps_morph_t:
+        if len(self.ops) > EPS_MORPH_MAX_OPS:
+            raise ValueError(f"at most {EPS_MORPH_MAX_OPS} operations")
+        m = eps_morph_t()
+        m.alpha = self.alpha
+        m.radius = self.radius
+        m.n_ops = len(self.ops)
+        for k, op in enumerate(self.ops):
+            m.ops[k] = int(op)
+        return m
+
+
+def eps_morph_workspace_size(prob: Problem, morph: Morph, n_lambda: int = 1) -> int:
+    n = ctypes.c_size_t(0)
+    p, m = prob.c_struct(), morph.c_struct()
+    _check(lib().eps_morph_workspace_size(ctypes.byref(p), ctypes.byref(m), n_lambda,
+                                          ctypes.byref(n)), "eps_morph_workspace_size")
+    return n.value
+
+
+def _morph_ws(prob, morph, ws, device):
+    import torch
+    need = eps_morph_workspace_size(prob, morph)
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
+    return ws
+
+
+def eps_forward_morph(prob: Problem, morph: Morph, C, eps=None, offdiag=None, ws=None, stream=None):
+    """eps_hat of the chain with morphology (Eq. 2-6, then the Yee stage).
+    Returns eps, or (eps, offdiag) when prob.flags has EPS_FLAG_OFFDIAG."""
+    import torch
+    _need(C, (prob.mx, prob.my), torch.float32, "C")
+    shape = (3, prob.nx, prob.ny, prob.nz)
+    if eps is None:
+        eps = torch.empty(shape, dtype=torch.float32, device=C.device)
+    _need(eps, shape, torch.float32, "eps")
+    want_od = bool(prob.flags & EPS_FLAG_OFFDIAG)
+    if want_od and offdiag is None:
+        offdiag = torch.empty((2,) + shape[1:], dtype=torch.float32, device=C.device)
+    ws = _morph_ws(prob, morph, ws, C.device)
+    p, m = prob.c_struct(), morph.c_struct()
+    _check(lib().eps_forward_morph(ctypes.byref(p), ctypes.byref(m), _ptr(C), _ptr(eps),
+                                   _ptr(offdiag) if want_od else None, _ptr(ws), ws.numel(),
+                                   _stream(stream)), "eps_forward_morph")
+    return (eps, offdiag) if want_od else eps
+
+
+def eps_vjp_morph(prob: Problem, morph: Morph, C, EF, EA, scale: float = -2.0, dJdC=None,
+                  eps_out=None, field_scales=None, ws=None, stream=None):
+    """Eq. 1 through the chain with morphology (complex64 fields).  Returns
+    dJdC, or (dJdC, eps_out) when eps_out is given (True allocates it)."""
+    import torch
+    _need(C, (prob.mx, prob.my), torch.float32, "C")
+    if len(EF) != len(EA):
+        raise ValueError("EF and EA must have the same number of wavelengths")
+    nl = len(EF)
+    if nl > EPS_MAX_LAMBDA:
+        raise ValueError(f"at most {EPS_MAX_LAMBDA} wavelengths per call")
+    for l in range(nl):
+        _need(EF[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EF[{l}]")
+        _need(EA[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EA[{l}]")
+    if dJdC is None:
+        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=C.device)
+    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC")
+    ret_eps = eps_out is not None and eps_out is not False
+    if eps_out is True:
+        eps_out = torch.empty((3, prob.nx, prob.ny, prob.nz), dtype=torch.float32, device=C.device)
+    if ret_eps:
+        _need(eps_out, (3, prob.nx, prob.ny, prob.nz), torch.float32, "eps_out")
+    ws = _morph_ws(prob, morph, ws, C.device)
+    ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
+    ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
+    fs = None
+    if field_scales is not None:
+        flat = [float(v) for v in _flatten(field_scales)]
+        if len(flat) != 6 * nl:
+            raise ValueError("field_scales must hold n_lambda x 2 x 3 values")
+        fs = (ctypes.c_float * len(flat))(*flat)
+    p, m = prob.c_struct(), morph.c_struct()
+    _check(lib().eps_vjp_morph(ctypes.byref(p), ctypes.byref(m), _ptr(C), nl, EPS_FIELD_C64, ef, ea,
+                               fs, float(scale), _ptr(dJdC), _ptr(eps_out) if ret_eps else None,
+                               _ptr(ws), ws.numel(), _stream(stream)), "eps_vjp_morph")
+    return (dJdC, eps_out) if ret_eps else dJdC
+
+
+def eps_vjp_real_morph(prob: Problem, morph: Morph, C, G, dJdC=None, ws=None, stream=None):
+    """(d eps_hat / dC)^T G through the chain with morphology."""
+    import torch
+    _need(C, (prob.mx, prob.my), torch.float32, "C")
+    _need(G, (3, prob.nx, prob.ny, prob.nz), torch.float32, "G")
+    if dJdC is None:
+        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=C.device)
+    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC")
+    ws = _morph_ws(prob, morph, ws, C.device)
+    p, m = prob.c_struct(), morph.c_struct()
+    _check(lib().eps_vjp_real_morph(ctypes.byref(p), ctypes.byref(m), _ptr(C), _ptr(G), _ptr(dJdC),
+                                    _ptr(ws), ws.numel(), _stream(stream)), "eps_vjp_real_morph")
+    return dJdC

@@ -157,3 +157,68 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(ec, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         ec.lib()
+
+
+# ------------------------------------------------------------ morphology path
+
+def test_morph_workspace_layout(L):
+    p = prob(mx=600, my=600, nz=24)
+    m = ec.Morph(alpha=20.0, radius=2.0)
+    al = lambda b: (b + 255) // 256 * 256
+    base = ec.eps_workspace_size(p)        # the Yee stage runs on rho_n with the same shapes
+    maps = (len(m.ops) + 4) * al(600 * 600 * 4)   # rho_0..rho_n, P'(u), two adjoint maps
+    assert ec.eps_morph_workspace_size(p, m) == maps + base
+    assert ec.eps_morph_workspace_size(p, ec.Morph(ops=())) == 4 * al(600 * 600 * 4) + base
+    assert ec.eps_morph_workspace_size(prob(mx=0), m) == 0
+
+
+def _morph_code(L, p, m):
+    n = ctypes.c_size_t()
+    return L.eps_morph_workspace_size(ctypes.byref(p.c_struct()), ctypes.byref(m), 1,
+                                      ctypes.byref(n))
+
+
+def test_bad_morphology_is_rejected_on_host(L):
+    p = prob()
+
+    def code(alpha=20.0, radius=2.0, ops=(0, 1)):
+        m = ec.eps_morph_t()
+        m.alpha, m.radius, m.n_ops = alpha, radius, len(ops)
+        for k, op in enumerate(ops[:8]):
+            m.ops[k] = op
+        return _morph_code(L, p, m)
+
+    assert code() == 0
+    assert code(alpha=0.0) == 1
+    assert code(alpha=float("nan")) == 1
+    assert code(alpha=61.0) == 1
+    assert code(radius=-0.5) == 1
+    assert code(radius=12.0) == 4        # disk larger than the built stencils
+    assert code(radius=11.99) == 0
+    assert code(ops=(0, 2)) == 1
+    m = ec.eps_morph_t()
+    m.alpha, m.radius, m.n_ops = 20.0, 2.0, 9
+    assert _morph_code(L, p, m) == 1
+    # the problem itself is validated first
+    assert _morph_code(L, prob(mx=63), ec.Morph().c_struct()) == 2
+    with pytest.raises(ValueError):
+        ec.Morph(ops=(0,) * 9).c_struct()
+
+
+def test_morph_entry_points_reject_bad_pointers_before_launch(L):
+    p = prob()
+    P = ctypes.byref(p.c_struct())
+    M = ctypes.byref(ec.Morph().c_struct())
+    fake = ctypes.c_void_p(0x10000)
+    assert L.eps_forward_morph(P, M, None, None, None, fake, 1 << 30, None) == 1
+    assert L.eps_forward_morph(P, M, fake, fake, None, fake, 16, None) == 3
+    assert L.eps_vjp_real_morph(P, M, fake, None, fake, fake, 1 << 30, None) == 1
+    arr = (ctypes.c_void_p * 1)(fake)
+    assert L.eps_vjp_morph(P, M, fake, 1, 0, arr, arr, None, -2.0, fake, None, fake, 16,
+                           None) == 3
+    assert L.eps_vjp_morph(P, M, fake, 1, 0, arr, arr, None, -2.0, fake, None,
+                           ctypes.c_void_p(0x10040), 1 << 30, None) == 3   # not 256-aligned
+    assert L.eps_vjp_morph(P, M, fake, 1, 7, arr, arr, None, -2.0, fake, None, fake, 1 << 30,
+                           None) == 1
+    assert L.eps_vjp_morph(P, None, fake, 1, 0, arr, arr, None, -2.0, fake, None, fake, 1 << 30,
+                           None) == 1
