@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--variant-set", default="cfg3,cfg4,cfg5,morph,opt",
+                    help="comma-separated variants to run (cfg3, cfg4, cfg5, morph, opt)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the cfg3 / batched cfg4 / reduced-precision cfg5 measurements")
     return ap.parse_args()
@@ -372,7 +374,8 @@ def run_ours(args, rank, world, local):
         cpu = cpu_baseline(w)
     variants = None
     if rank == 0 and world == 1 and not args.no_variants:
-        variants = run_variants(torch, ec, synth, dev, flush_l2)
+        variants = run_variants(torch, ec, synth, dev, flush_l2,
+                                set(args.variant_set.split(",")))
 
     if rank == 0:
         line = {
@@ -452,88 +455,140 @@ def _window_error(w, C, EF, EA, g_gpu, half=48):
     return worst
 
 
-def run_variants(torch, ec, synth, dev, flush_l2):
+def run_variants(torch, ec, synth, dev, flush_l2, sel=("cfg3", "cfg4", "cfg5", "morph")):
     """The differentiation (cfg3), batching (cfg4) and precision (cfg5) forms,
     each timed like the main workload (L2 flushed before every call)."""
     out = {}
     peak, _ = measured_peaks()
 
-    # cfg3: 2000 x 2000 controls, 1000 x 1000 x 32, three wavelengths
-    w = synth.WORKLOADS[3]
-    p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
-    C = torch.from_numpy(synth.controls(w)).to(dev)
-    EF = _device_fields(torch, (3, w.nx, w.ny, w.nz), 3, 2030, dev)
-    EA = _device_fields(torch, (3, w.nx, w.ny, w.nz), 3, 3030, dev)
-    G = torch.empty((w.mx, w.my), device=dev)
-    E = torch.empty((3, w.nx, w.ny, w.nz), device=dev)
-    call = ec.PreparedVjp(p, C, EF, EA, G, eps_out=E)
-    ms = _timed(call, flush_l2, 20, torch)
-    alg = algorithmic_bytes(w, 3)
-    out["cfg3_fp32_3wavelengths"] = {"workload": w.name, "value": w.voxels / (ms * 1e-3),
-                                     "unit": UNIT, "ms_per_call": round(ms, 4),
-                                     "whole_call_hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4)}
-    del C, EF, EA, G, E, call
+    if "cfg3" in sel:
+        # cfg3: 2000 x 2000 controls, 1000 x 1000 x 32, three wavelengths
+        w = synth.WORKLOADS[3]
+        p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+        C = torch.from_numpy(synth.controls(w)).to(dev)
+        EF = _device_fields(torch, (3, w.nx, w.ny, w.nz), 3, 2030, dev)
+        EA = _device_fields(torch, (3, w.nx, w.ny, w.nz), 3, 3030, dev)
+        G = torch.empty((w.mx, w.my), device=dev)
+        E = torch.empty((3, w.nx, w.ny, w.nz), device=dev)
+        call = ec.PreparedVjp(p, C, EF, EA, G, eps_out=E)
+        ms = _timed(call, flush_l2, 20, torch)
+        alg = algorithmic_bytes(w, 3)
+        out["cfg3_fp32_3wavelengths"] = {"workload": w.name, "value": w.voxels / (ms * 1e-3),
+                                         "unit": UNIT, "ms_per_call": round(ms, 4),
+                                         "whole_call_hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4)}
+        del C, EF, EA, G, E, call
 
-    # cfg4: 64 regions of uneven size, radius and beta; batched vs per region
-    regs = synth.batched_regions()
-    probs, Cs, EFs, EAs = [], [], [], []
-    for r, rw in enumerate(regs):
-        probs.append(ec.Problem(mx=rw.mx, my=rw.my, nz=rw.nz, radius=rw.radius, beta=rw.beta))
-        Cs.append(torch.from_numpy(synth.soi_layout(rw.mx, rw.my, 1004 * 1000 + r)).to(dev))
-        EFs.append(_device_fields(torch, (3, rw.nx, rw.ny, rw.nz), 1, 2040 * 1000 + r, dev))
-        EAs.append(_device_fields(torch, (3, rw.nx, rw.ny, rw.nz), 1, 3040 * 1000 + r, dev))
-    vox = sum(rw.voxels for rw in regs)
-    bv = ec.BatchedVjp(probs, Cs, EFs, EAs)
-    bv()
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
+    if "cfg4" in sel:
+        # cfg4: 64 regions of uneven size, radius and beta; batched vs per region
+        regs = synth.batched_regions()
+        probs, Cs, EFs, EAs = [], [], [], []
+        for r, rw in enumerate(regs):
+            probs.append(ec.Problem(mx=rw.mx, my=rw.my, nz=rw.nz, radius=rw.radius, beta=rw.beta))
+            Cs.append(torch.from_numpy(synth.soi_layout(rw.mx, rw.my, 1004 * 1000 + r)).to(dev))
+            EFs.append(_device_fields(torch, (3, rw.nx, rw.ny, rw.nz), 1, 2040 * 1000 + r, dev))
+            EAs.append(_device_fields(torch, (3, rw.nx, rw.ny, rw.nz), 1, 3040 * 1000 + r, dev))
+        vox = sum(rw.voxels for rw in regs)
+        bv = ec.BatchedVjp(probs, Cs, EFs, EAs)
         bv()
-    ms_b = _timed(graph.replay, flush_l2, 20, torch)
-    singles = [ec.PreparedVjp(p, C, ef, ea, G, eps_out=E)
-               for p, C, ef, ea, G, E in zip(probs, Cs, EFs, EAs, bv.dJdC, bv.eps)]
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            bv()
+        ms_b = _timed(graph.replay, flush_l2, 20, torch)
+        singles = [ec.PreparedVjp(p, C, ef, ea, G, eps_out=E)
+                   for p, C, ef, ea, G, E in zip(probs, Cs, EFs, EAs, bv.dJdC, bv.eps)]
 
-    def per_region():
-        for c in singles:
-            c()
+        def per_region():
+            for c in singles:
+                c()
 
-    ms_s = _timed(per_region, flush_l2, 20, torch)
-    out["cfg4_batched_64_regions"] = {
-        "regions": len(regs), "voxels": vox, "value": vox / (ms_b * 1e-3), "unit": UNIT,
-        "ms_per_call": round(ms_b, 4), "per_region_launches": {
-            "value": vox / (ms_s * 1e-3), "ms_per_call": round(ms_s, 4)},
-        "speedup_vs_per_region": round(ms_s / ms_b, 3),
-        "launch": "one CUDA graph: 1 contraction + 1 stencil and 1 scatter launch per radius group"}
-    del bv, graph, singles, Cs, EFs, EAs
+        ms_s = _timed(per_region, flush_l2, 20, torch)
+        out["cfg4_batched_64_regions"] = {
+            "regions": len(regs), "voxels": vox, "value": vox / (ms_b * 1e-3), "unit": UNIT,
+            "ms_per_call": round(ms_b, 4), "per_region_launches": {
+                "value": vox / (ms_s * 1e-3), "ms_per_call": round(ms_s, 4)},
+            "speedup_vs_per_region": round(ms_s / ms_b, 3),
+            "launch": "one CUDA graph: 1 contraction + 1 stencil and 1 scatter launch per radius group"}
+        del bv, graph, singles, Cs, EFs, EAs
 
-    # cfg5: 3000 x 3000, 1500 x 1500 x 32, eight wavelengths; FP32 / BF16 / FP16 fields
-    w = synth.WORKLOADS[5]
-    p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
-    Ch = synth.controls(w)
-    C = torch.from_numpy(Ch).to(dev)
-    EF = _device_fields(torch, (3, w.nx, w.ny, w.nz), 8, 2050, dev)
-    EA = _device_fields(torch, (3, w.nx, w.ny, w.nz), 8, 3050, dev)
-    G = torch.empty((w.mx, w.my), device=dev)
-    E = torch.empty((3, w.nx, w.ny, w.nz), device=dev)
-    res = {}
-    call = ec.PreparedVjp(p, C, EF, EA, G, eps_out=E)
-    ms = _timed(call, flush_l2, 10, torch)
-    err = _window_error(w, Ch, EF, EA, G.cpu().numpy())
-    res["fp32"] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
-                   "algorithmic_bytes": algorithmic_bytes(w, 8),
-                   "dJdC_max_err_vs_fp64_oracle": err}
-    for name, ft in (("bf16", ec.EPS_FIELD_BF16X2_SCALED), ("fp16", ec.EPS_FIELD_F16X2_SCALED)):
-        PF = [ec.eps_field_pack(p, ft, e) for e in EF]
-        PA = [ec.eps_field_pack(p, ft, e) for e in EA]
-        call = ec.PreparedVjp(p, C, PF, PA, G, eps_out=E, field_type=ft)
+    if "cfg5" in sel:
+        # cfg5: 3000 x 3000, 1500 x 1500 x 32, eight wavelengths; FP32 / BF16 / FP16 fields
+        w = synth.WORKLOADS[5]
+        p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+        Ch = synth.controls(w)
+        C = torch.from_numpy(Ch).to(dev)
+        EF = _device_fields(torch, (3, w.nx, w.ny, w.nz), 8, 2050, dev)
+        EA = _device_fields(torch, (3, w.nx, w.ny, w.nz), 8, 3050, dev)
+        G = torch.empty((w.mx, w.my), device=dev)
+        E = torch.empty((3, w.nx, w.ny, w.nz), device=dev)
+        res = {}
+        call = ec.PreparedVjp(p, C, EF, EA, G, eps_out=E)
         ms = _timed(call, flush_l2, 10, torch)
         err = _window_error(w, Ch, EF, EA, G.cpu().numpy())
-        alg = 8 * w.mx * w.my + 12 * w.nx * w.ny * w.nz + w.nx * w.ny * 8 * (3 * w.slab_nk + 1) * 2 * 4
-        res[name] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
-                     "algorithmic_bytes": alg, "dJdC_max_err_vs_fp64_oracle": err,
-                     "packed_bytes_per_field": ec.eps_packed_field_bytes(p, ft)}
-        del PF, PA, call
-    out["cfg5_precision_8wavelengths"] = dict(workload=w.name, unit=UNIT, **res)
+        res["fp32"] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
+                       "algorithmic_bytes": algorithmic_bytes(w, 8),
+                       "dJdC_max_err_vs_fp64_oracle": err}
+        for name, ft in (("bf16", ec.EPS_FIELD_BF16X2_SCALED), ("fp16", ec.EPS_FIELD_F16X2_SCALED)):
+            PF = [ec.eps_field_pack(p, ft, e) for e in EF]
+            PA = [ec.eps_field_pack(p, ft, e) for e in EA]
+            call = ec.PreparedVjp(p, C, PF, PA, G, eps_out=E, field_type=ft)
+            ms = _timed(call, flush_l2, 10, torch)
+            err = _window_error(w, Ch, EF, EA, G.cpu().numpy())
+            alg = 8 * w.mx * w.my + 12 * w.nx * w.ny * w.nz + w.nx * w.ny * 8 * (3 * w.slab_nk + 1) * 2 * 4
+            res[name] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
+                         "algorithmic_bytes": alg, "dJdC_max_err_vs_fp64_oracle": err,
+                         "packed_bytes_per_field": ec.eps_packed_field_bytes(p, ft)}
+            del PF, PA, call
+        out["cfg5_precision_8wavelengths"] = dict(workload=w.name, unit=UNIT, **res)
+        del C, EF, EA, G, E
+    if "morph" in sel:
+        out["cfg2_morphology"] = run_morph_variant(torch, ec, synth, dev, flush_l2)
+    if "opt" in sel:
+        out["optimizer_step"] = run_opt_variant(torch, ec, synth, dev, flush_l2)
+    return out
+
+
+def run_opt_variant(torch, ec, synth, dev, flush_l2):
+    """One on-device optimiser iteration (Adam + gray count + Eq. 14-15) on
+    the cfg2 and cfg5 control grids, L2 flushed before each call: an
+    HBM-bound elementwise kernel with 32 algorithmic bytes per control (C, M,
+    V read and written, G and the VJP's per-subpixel factor read)."""
+    import ctypes
+    peak, _ = measured_peaks()
+    out = {}
+    for cfg in (2, 5):
+        w = synth.WORKLOADS[cfg]
+        p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+        C = torch.from_numpy(synth.controls(w)).to(dev)
+        EF = _device_fields(torch, (3, w.nx, w.ny, w.nz), 1, 2000 + 10 * cfg, dev)
+        EA = _device_fields(torch, (3, w.nx, w.ny, w.nz), 1, 3000 + 10 * cfg, dev)
+        ws = torch.empty(ec.eps_workspace_size(p), dtype=torch.uint8, device=dev)
+        G = ec.eps_vjp(p, C, EF, EA, ws=ws)      # fills the workspace for the gray count
+        del EF, EA
+        M, V = torch.zeros_like(C), torch.zeros_like(C)
+        # tiny steps keep the design (and so the VJP workspace) meaningful
+        opt = ec.OptParams(lr=1e-9, beta_min=w.beta, beta_max0=w.beta, n_iter=1 << 30)
+        state = ec.eps_opt_init(opt)
+        pc, oc = p.c_struct(), opt.c_struct()
+        fn = ec.lib().eps_opt_step
+        args = (ctypes.byref(pc), None, ctypes.byref(oc), ctypes.c_void_p(state.data_ptr()),
+                ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(G.data_ptr()),
+                ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                ctypes.c_void_p(ws.data_ptr()), ws.numel())
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+        def call():
+            fn(*args, stream)
+
+        ms = _timed(call, flush_l2, 100, torch)
+        ec.eps_sync_status()
+        st = ec.read_opt_state(state)
+        alg = 32 * w.mx * w.my
+        gbs = alg / (ms * 1e-3) / 1e9
+        out[w.name] = {"controls": w.mx * w.my, "us_per_call": round(ms * 1e3, 2),
+                       "algorithmic_bytes": alg, "achieved_gbs": round(gbs, 1),
+                       "hbm_frac": round(gbs / peak, 4), "gray_fraction": round(st["unbinarity"], 5)}
+        del C, ws, G, M, V
     return out
 
 

@@ -246,6 +246,63 @@ eps_status_t eps_vjp_real_morph(const eps_problem_t *prob, const eps_morph_t *mo
                                 size_t ws_bytes, eps_stream_t stream);
 
 /*
+ * One optimiser iteration on the device (Sec. 4): Adam (Eq. 10-11) over the
+ * controls, fused with the count of gray subpixels of the design, then the
+ * beta_max control (Eq. 15) and the beta schedule (Eq. 14).
+ *
+ * Readings (the paper is silent): a subpixel is gray when its projected
+ * density rho satisfies gray_tol < rho < 1 - gray_tol; the unbinarity is
+ * u = max(gray count, 1) / (mx my); t starts at its first sample
+ * (1/u - 1)/beta, then t <- gamma t + (1 - gamma)(1/u - 1)/beta and
+ * beta_max <- gamma beta_max + (1 - gamma)(1/u0 - 1)/t; iteration i is
+ * 1-based, the same i as Adam's bias correction, and the beta of iteration
+ * i is beta_min + (beta_max - beta_min)(exp((i/n_iter)^2) - 1)/(e - 1).
+ *
+ * eps_opt_t (host):  lr (the paper's eta), b1, b2, adam_eps, gray_tol in
+ *   (0, 1/2), gamma in [0, 1), u0 in (0, 1), beta_min > 0,
+ *   beta_max0 >= beta_min (initial beta_max), n_iter >= 1 (N_i).
+ *   App. B: b1 = 0.9, b2 = 0.999, lr = 0.001, gamma = 0.95, u0 = 0.01,
+ *   beta_min = 10.
+ * eps_opt_state_t (DEVICE memory, 32 bytes, 4-byte aligned, caller-owned):
+ *   step        completed iterations (the next is step + 1)
+ *   beta        beta of the next iteration: pass it as prob->beta of the
+ *               next eps_vjp call (read it back, or keep the loop on the
+ *               device with the same value)
+ *   beta_max, t the Eq. 15 state;  unbinarity, gray: u and the gray count
+ *               of the last iteration;  gray_acc, ticket: scratch, zero
+ *               between calls.
+ * eps_opt_init writes the initial state (step 0, beta of iteration 1,
+ *   beta_max0) with a kernel on `stream`.
+ * eps_opt_step performs iteration step + 1:
+ *   prob, morph   the problem (and the morphology, or NULL) of the eps_vjp /
+ *                 eps_vjp_real / eps_vjp_morph / eps_vjp_real_morph call
+ *                 whose workspace `ws` (ws_bytes) holds the design of C at
+ *                 beta = prob->beta; prob->beta must equal state->beta, be
+ *                 > 0, and eps_core must differ from eps_clad.  The gray
+ *                 count reads the per-subpixel factor that call left there.
+ *   C, M, V       device float32 [mx][my], 16-byte aligned, updated in place
+ *                 (M and V start at zero)
+ *   G             device float32 [mx][my], 16-byte aligned: the gradient of
+ *                 the objective being minimised at C
+ * Successive steps on one state must be ordered on one stream.
+ */
+typedef struct {
+  float lr, b1, b2, adam_eps, gray_tol, gamma, u0, beta_min, beta_max0;
+  int32_t n_iter;
+} eps_opt_t;
+
+typedef struct {
+  int32_t step;
+  float beta, beta_max, t, unbinarity;
+  uint32_t gray, gray_acc, ticket;
+} eps_opt_state_t;
+
+eps_status_t eps_opt_init(const eps_opt_t *opt, eps_opt_state_t *state, eps_stream_t stream);
+eps_status_t eps_opt_step(const eps_problem_t *prob, const eps_morph_t *morph, const eps_opt_t *opt,
+                          eps_opt_state_t *state, float *C, const float *G, float *M, float *V,
+                          const void *ws, size_t ws_bytes, eps_stream_t stream);
+
+/*
  * Synchronise `stream`, then return (and clear) any device-side error flag
  * raised by earlier calls on this device: EPS_ERR_DEVICE_TIMEOUT or
  * EPS_ERR_DEVICE_BOUNDS, else EPS_OK; EPS_ERR_CUDA if the sync failed.

@@ -15,7 +15,8 @@ from .epschain import (BatchedVjp, eps_batched_workspace_size, eps_forward_batch
                        eps_vjp, eps_vjp_real, eps_workspace_size, lib,
                        CLOSE_THEN_OPEN, EPS_MORPH_DILATE, EPS_MORPH_ERODE, Morph,
                        eps_forward_morph, eps_morph_workspace_size, eps_vjp_morph,
-                       eps_vjp_real_morph)
+                       eps_vjp_real_morph, PreparedVjpMorph,
+                       OptParams, eps_opt_init, eps_opt_step, read_opt_state)
 
 __all__ = [
     "BatchedVjp", "eps_batched_workspace_size", "eps_forward_batched",
@@ -26,7 +27,8 @@ __all__ = [
     "eps_sync_status", "eps_vjp",
     "eps_vjp_real", "eps_workspace_size", "lib",
     "CLOSE_THEN_OPEN", "EPS_MORPH_DILATE", "EPS_MORPH_ERODE", "Morph", "eps_forward_morph",
-    "eps_morph_workspace_size", "eps_vjp_morph", "eps_vjp_real_morph",
+    "eps_morph_workspace_size", "eps_vjp_morph", "eps_vjp_real_morph", "PreparedVjpMorph",
+    "OptParams", "eps_opt_init", "eps_opt_step", "read_opt_state",
 ]
 
 from . import autograd  # noqa: E402  (torch.autograd wrappers)

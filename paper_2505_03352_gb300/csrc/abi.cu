@@ -998,4 +998,16 @@ eps_status_t launch_kernel(const char *name, const void *fn, dim3 grid, size_t s
   return launch(name, fn, grid, smem, args, s, pdl);
 }
 
+eps_status_t subpixel_factor_offset(const eps_problem_t *prob, size_t *offset, size_t *ws_needed) {
+  Resolved r;
+  const eps_status_t st = resolve(prob, &r);
+  if (st != EPS_OK) return st;
+  const WsLayout L = ws_layout(r.g);
+  *offset = L.pd4;
+  *ws_needed = r.empty ? 0 : L.total;
+  return EPS_OK;
+}
+
+eps_status_t sm_count_current(int *n) { return sm_count(n); }
+
 }  // namespace epsc_host

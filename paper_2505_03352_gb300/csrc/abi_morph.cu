@@ -113,7 +113,9 @@ eps_status_t run_map(const char *name, int kind, int rp1, const float *w, const 
   std::memcpy(ma.w, w, sizeof(ma.w));
   const KernelEntry k = map_entry(rp1, prob->bc, kind);
   const dim3 grid((prob->my + MT_B - 1) / MT_B, (prob->mx + MT_A - 1) / MT_A);
-  return epsc_host::launch_kernel(name, k.fn, grid, k.smem, &ma, s, false);
+  // programmatic dependent launch: the kernel waits for the previous grid
+  // before touching global memory
+  return epsc_host::launch_kernel(name, k.fn, grid, k.smem, &ma, s, true);
 }
 
 // C -> rho_0, P'(u) -> rho_1 .. rho_n
@@ -222,3 +224,17 @@ eps_status_t eps_vjp_real_morph(const eps_problem_t *prob, const eps_morph_t *mo
 }
 
 }  // extern "C"
+
+namespace epsc_host {
+
+eps_status_t morph_base_offset(const eps_problem_t *prob, const eps_morph_t *morph, size_t *offset,
+                               size_t *ws_needed) {
+  MorphPlan P;
+  const eps_status_t st = plan(prob, morph, &P);
+  if (st != EPS_OK) return st;
+  *offset = P.yee_off;
+  *ws_needed = P.total;
+  return EPS_OK;
+}
+
+}  // namespace epsc_host

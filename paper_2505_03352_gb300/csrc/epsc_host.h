@@ -25,4 +25,17 @@ eps_status_t check_vjp_args(const eps_problem_t *prob, const float *C, int32_t n
 eps_status_t launch_kernel(const char *name, const void *fn, dim3 grid, size_t smem, void *args,
                            cudaStream_t s, bool pdl);
 
+// Byte offset, inside an eps_vjp / eps_vjp_real workspace for `prob`, of
+// the per-subpixel factor (beta/2)(eps_core - eps_clad) rho (1 - rho)
+// [mx][my] that the stencil pass writes, and the workspace size.
+eps_status_t subpixel_factor_offset(const eps_problem_t *prob, size_t *offset, size_t *ws_needed);
+
+// Byte offset of the base chain's workspace inside an eps_vjp_morph
+// workspace, and the morphology workspace size.
+eps_status_t morph_base_offset(const eps_problem_t *prob, const eps_morph_t *morph, size_t *offset,
+                               size_t *ws_needed);
+
+// Multiprocessor count of the current device.
+eps_status_t sm_count_current(int *n);
+
 }  // namespace epsc_host

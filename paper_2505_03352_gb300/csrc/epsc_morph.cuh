@@ -81,7 +81,14 @@ __global__ void __launch_bounds__(NTHREADS) map_kernel(const __grid_constant__ M
   const int SA_USED = NSTRIP * NA_M + 2 * R;
   const int SB_USED = GB + 2 * R;
 
+  // Launched behind the previous kernel of the chain (programmatic dependent
+  // launch): let the next one start launching, then wait for the previous
+  // grid's results before the first global read or write.
+  griddep_launch_dependents();
+  griddep_wait();
+
   // ---- stage the (transformed) input with its halo ----------------------
+#pragma unroll 4
   for (int idx = tid; idx < SA_USED * SB_USED; idx += NTHREADS) {
     const int r = idx / SB_USED, c = idx - r * SB_USED;
     int x = ga_lo - R + r, y = gb_lo - R + c;

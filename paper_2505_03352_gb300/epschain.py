@@ -122,6 +122,9 @@ _PROTOS = {
                                      ctypes.c_size_t, _VP]),
     "eps_vjp_real_morph": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP,
                                           ctypes.c_size_t, _VP]),
+    "eps_opt_init": (ctypes.c_int, [_VP, _VP, _VP]),
+    "eps_opt_step": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP, _VP,
+                                    _VP, _VP, ctypes.c_size_t, _VP]),
 }
 
 
@@ -547,3 +550,93 @@ def eps_vjp_real_morph(prob: Problem, morph: Morph, C, G, dJdC=None, ws=None, st
     _check(lib().eps_vjp_real_morph(ctypes.byref(p), ctypes.byref(m), _ptr(C), _ptr(G), _ptr(dJdC),
                                     _ptr(ws), ws.numel(), _stream(stream)), "eps_vjp_real_morph")
     return dJdC
+
+
+class PreparedVjpMorph:
+    """eps_vjp_morph with its ctypes arguments built once (complex64 fields)."""
+
+    def __init__(self, prob: Problem, morph: Morph, C, EF, EA, dJdC, eps_out=None, ws=None,
+                 scale=-2.0):
+        nl = len(EF)
+        self._keep = (C, list(EF), list(EA), dJdC, eps_out)
+        if ws is None:
+            ws = _morph_ws(prob, morph, None, C.device)
+        self._ws = ws
+        self._p, self._m = prob.c_struct(), morph.c_struct()
+        self._ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
+        self._ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
+        self._args = (ctypes.byref(self._p), ctypes.byref(self._m), _ptr(C), nl, EPS_FIELD_C64,
+                      self._ef, self._ea, None, float(scale), _ptr(dJdC), _ptr(eps_out), _ptr(ws),
+                      ws.numel())
+        self._fn = lib().eps_vjp_morph
+
+    def __call__(self, stream=None):
+        _check(self._fn(*self._args, _stream(stream)), "eps_vjp_morph")
+
+
+# ---------------------------------------------------------------- optimiser
+
+class eps_opt_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("lr", "b1", "b2", "adam_eps", "gray_tol", "gamma",
+                                               "u0", "beta_min", "beta_max0")] + \
+               [("n_iter", ctypes.c_int32)]
+
+
+OPT_STATE_FIELDS = ("step", "beta", "beta_max", "t", "unbinarity", "gray", "gray_acc", "ticket")
+
+
+@dataclass(frozen=True)
+class OptParams:
+    """Adam (Eq. 10-11) with the beta schedule and beta_max control (Eq.
+    14-15); App. B defaults.  gray_tol: a subpixel with gray_tol < rho <
+    1 - gray_tol counts as gray."""
+
+    lr: float = 0.001
+    b1: float = 0.9
+    b2: float = 0.999
+    adam_eps: float = 1e-8
+    gray_tol: float = 0.05
+    gamma: float = 0.95
+    u0: float = 0.01
+    beta_min: float = 10.0
+    beta_max0: float = 100.0
+    n_iter: int = 100
+
+    def c_struct(self) -> eps_opt_t:
+        o = eps_opt_t()
+        for f in ("lr", "b1", "b2", "adam_eps", "gray_tol", "gamma", "u0", "beta_min", "beta_max0"):
+            setattr(o, f, getattr(self, f))
+        o.n_iter = self.n_iter
+        return o
+
+
+def eps_opt_init(opt: OptParams, state=None, device=None, stream=None):
+    """Device optimiser state (a 32-byte uint8 tensor) set to iteration 0."""
+    import torch
+    if state is None:
+        state = torch.zeros(32, dtype=torch.uint8, device=device or "cuda")
+    o = opt.c_struct()
+    _check(lib().eps_opt_init(ctypes.byref(o), _ptr(state), _stream(stream)), "eps_opt_init")
+    return state
+
+
+def read_opt_state(state) -> dict:
+    """The device state as a dict (copies 32 bytes to the host; synchronises)."""
+    import struct
+    b = bytes(state.cpu().numpy().tobytes())
+    vals = struct.unpack("<i4f3I", b)
+    return dict(zip(OPT_STATE_FIELDS, vals))
+
+
+def eps_opt_step(prob: Problem, opt: OptParams, state, C, G, M, V, ws, morph=None, stream=None):
+    """Iteration state.step + 1 in place on C, M, V; `ws` is the workspace of
+    the VJP call (base chain, or morphology when `morph` is given) that
+    evaluated C at beta = prob.beta."""
+    import torch
+    for name, t in (("C", C), ("G", G), ("M", M), ("V", V)):
+        _need(t, (prob.mx, prob.my), torch.float32, name)
+    p, o = prob.c_struct(), opt.c_struct()
+    m = morph.c_struct() if morph is not None else None
+    _check(lib().eps_opt_step(ctypes.byref(p), ctypes.byref(m) if m is not None else None,
+                              ctypes.byref(o), _ptr(state), _ptr(C), _ptr(G), _ptr(M), _ptr(V),
+                              _ptr(ws), ws.numel(), _stream(stream)), "eps_opt_step")

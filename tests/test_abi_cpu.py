@@ -222,3 +222,33 @@ def test_morph_entry_points_reject_bad_pointers_before_launch(L):
                            None) == 1
     assert L.eps_vjp_morph(P, None, fake, 1, 0, arr, arr, None, -2.0, fake, None, fake, 1 << 30,
                            None) == 1
+
+
+# ------------------------------------------------------------- optimiser step
+
+def test_bad_optimiser_parameters_are_rejected_on_host(L):
+    p = prob()
+    fake = ctypes.c_void_p(0x10000)
+
+    def code(**kw):
+        o = ec.OptParams(**kw).c_struct()
+        return L.eps_opt_step(ctypes.byref(p.c_struct()), None, ctypes.byref(o), fake, fake, fake,
+                              fake, fake, fake, 16, None)
+
+    assert code(lr=0.0) == 1
+    assert code(b1=1.0) == 1
+    assert code(b2=-0.1) == 1
+    assert code(gray_tol=0.5) == 1
+    assert code(gamma=1.0) == 1
+    assert code(u0=0.0) == 1
+    assert code(beta_min=0.0) == 1
+    assert code(beta_max0=5.0) == 1          # below beta_min
+    assert code(n_iter=0) == 1
+    assert code(adam_eps=float("nan")) == 1
+    assert code() == 3                         # valid parameters: the workspace is too small
+    o = ec.OptParams().c_struct()
+    assert L.eps_opt_init(ctypes.byref(o), None, None) == 1
+    assert L.eps_opt_step(ctypes.byref(prob(beta=-1.0).c_struct()), None, ctypes.byref(o), fake,
+                          fake, fake, fake, fake, fake, 1 << 30, None) == 1
+    assert L.eps_opt_step(ctypes.byref(p.c_struct()), None, ctypes.byref(o), fake,
+                          ctypes.c_void_p(0x10004), fake, fake, fake, fake, 1 << 30, None) == 1
