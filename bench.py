@@ -49,8 +49,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=40)
-    ap.add_argument("--variant-set", default="cfg3,cfg4,cfg5,morph,opt",
-                    help="comma-separated variants to run (cfg3, cfg4, cfg5, morph, opt)")
+    ap.add_argument("--variant-set", default="cfg3,cfg4,cfg5,morph,opt,coarse",
+                    help="comma-separated variants to run (cfg3, cfg4, cfg5, morph, opt, coarse)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the cfg3 / batched cfg4 / reduced-precision cfg5 measurements")
     return ap.parse_args()
@@ -545,7 +545,60 @@ def run_variants(torch, ec, synth, dev, flush_l2, sel=("cfg3", "cfg4", "cfg5", "
         out["cfg2_morphology"] = run_morph_variant(torch, ec, synth, dev, flush_l2)
     if "opt" in sel:
         out["optimizer_step"] = run_opt_variant(torch, ec, synth, dev, flush_l2)
+    if "coarse" in sel:
+        out["coarse_controls"] = run_coarse_variant(torch, ec, synth, dev, flush_l2)
     return out
+
+
+def run_coarse_variant(torch, ec, synth, dev, flush_l2):
+    """The paper's coarse parametrisation: a 210 x 210-cell design region
+    (420 x 420 subpixels, nz = 24, cfg2 slab) driven by 36 x 36 control nodes
+    (Eq. 2, hat basis), fused forward + VJP with one wavelength, checked
+    against the FP64 oracle."""
+    import ctypes
+    import numpy as np
+    from oracle import coarse_oracle as co
+    from oracle import epschain_oracle as orc
+    mx = my = 420
+    nz, ncx, ncy = 24, 36, 36
+    p = ec.Problem(mx=mx, my=my, nz=nz, radius=1.0, beta=16.0)
+    g = ec.Coarse(ncx, ncy)
+    ch = (0.5 + 0.35 * np.random.default_rng(1006).standard_normal((ncx, ncy))).astype(np.float32)
+    c = torch.from_numpy(ch).to(dev)
+    shape = (3, mx // 2, my // 2, nz)
+    EFh, EAh = [synth.complex_field(shape, 2006)], [synth.complex_field(shape, 3006)]
+    EF = [torch.from_numpy(e).to(dev) for e in EFh]
+    EA = [torch.from_numpy(e).to(dev) for e in EAh]
+    dc = torch.empty((ncx, ncy), device=dev)
+    E = torch.empty(shape, device=dev)
+    ws = torch.empty(ec.eps_coarse_workspace_size(p, g), dtype=torch.uint8, device=dev)
+    pc, gc = p.c_struct(), g.c_struct()
+    ef = (ctypes.c_void_p * 1)(EF[0].data_ptr())
+    ea = (ctypes.c_void_p * 1)(EA[0].data_ptr())
+    fn = ec.lib().eps_vjp_coarse
+    args = (ctypes.byref(pc), ctypes.byref(gc), ctypes.c_void_p(c.data_ptr()), 1, 0, ef, ea, None,
+            -2.0, ctypes.c_void_p(dc.data_ptr()), ctypes.c_void_p(E.data_ptr()),
+            ctypes.c_void_p(ws.data_ptr()), ws.numel())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call():
+        fn(*args, stream)
+
+    ms = _timed(call, flush_l2, 100, torch)
+    ec.eps_profile_start()
+    for _ in range(20):
+        flush_l2()
+        call()
+    prof = ec.eps_profile_stop()
+    ec.eps_sync_status()
+    o = orc.Problem(mx=mx, my=my, nz=nz, radius=1.0, beta=16.0)
+    ref = co.vjp_fields_coarse(o, ch, EFh, EAh)
+    err = float(np.max(np.abs(dc.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+    vox = (mx // 2) * (my // 2) * nz
+    return {"workload": "210x210x24 cells, 36x36 control nodes, beta 16, 1 wavelength",
+            "value": vox / (ms * 1e-3), "unit": UNIT, "ms_per_call": round(ms, 4),
+            "kernel_us_avg": {k: round(v[1] / v[0] * 1e3, 2) for k, v in prof.items()},
+            "dJdc_max_err_vs_fp64_oracle": err}
 
 
 def run_opt_variant(torch, ec, synth, dev, flush_l2):

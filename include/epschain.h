@@ -246,6 +246,41 @@ eps_status_t eps_vjp_real_morph(const eps_problem_t *prob, const eps_morph_t *mo
                                 size_t ws_bytes, eps_stream_t stream);
 
 /*
+ * Coarse control variables (Eq. 2 with the basis functions shifted to the
+ * nodes of a rectangular grid that spans the design region, as in the
+ * paper's 36 x 36 controls over 210 x 210 cells).  The node values c are
+ * float32 [ncx][ncy] (device); node i sits at X_i = i h_x, h_x =
+ * mx / (ncx - 1) subpixels (edge to edge), subpixel a's centre at a + 1/2,
+ * and the basis is the tensor-product hat B(t) = max(0, 1 - |t|) (a reading:
+ * compact, a partition of unity, exact on linear functions):
+ *   Phi[a][b] = sum_{i,j} c[i][j] B((a + 1/2 - X_i)/h_x) B((b + 1/2 - Y_j)/h_y).
+ * Phi replaces the conic filter's output: the base chain runs on Phi with
+ * an identity filter (prob->radius is validated but not used) and
+ * projection threshold prob->eta.  eps_vjp_coarse / eps_vjp_real_coarse
+ * have the arguments of eps_vjp / eps_vjp_real with dJdc float32
+ * [ncx][ncy] (device).  ncx, ncy >= 2.  Workspace: Phi, d/dPhi and the
+ * base chain's workspace, eps_coarse_workspace_size() bytes, 256-byte
+ * aligned.
+ */
+typedef struct {
+  int32_t ncx, ncy;
+} eps_coarse_t;
+
+eps_status_t eps_coarse_workspace_size(const eps_problem_t *prob, const eps_coarse_t *coarse,
+                                       int32_t n_lambda, size_t *bytes);
+eps_status_t eps_forward_coarse(const eps_problem_t *prob, const eps_coarse_t *coarse,
+                                const float *c, float *eps, float *offdiag, void *ws,
+                                size_t ws_bytes, eps_stream_t stream);
+eps_status_t eps_vjp_coarse(const eps_problem_t *prob, const eps_coarse_t *coarse, const float *c,
+                            int32_t n_lambda, int32_t field_type, const void *const *EF,
+                            const void *const *EA, const float *field_scales, float scale,
+                            float *dJdc, float *eps_out, void *ws, size_t ws_bytes,
+                            eps_stream_t stream);
+eps_status_t eps_vjp_real_coarse(const eps_problem_t *prob, const eps_coarse_t *coarse,
+                                 const float *c, const float *G, float *dJdc, void *ws,
+                                 size_t ws_bytes, eps_stream_t stream);
+
+/*
  * One optimiser iteration on the device (Sec. 4): Adam (Eq. 10-11) over the
  * controls, fused with the count of gray subpixels of the design, then the
  * beta_max control (Eq. 15) and the beta schedule (Eq. 14).

@@ -16,7 +16,9 @@ from .epschain import (BatchedVjp, eps_batched_workspace_size, eps_forward_batch
                        CLOSE_THEN_OPEN, EPS_MORPH_DILATE, EPS_MORPH_ERODE, Morph,
                        eps_forward_morph, eps_morph_workspace_size, eps_vjp_morph,
                        eps_vjp_real_morph, PreparedVjpMorph,
-                       OptParams, eps_opt_init, eps_opt_step, read_opt_state)
+                       OptParams, eps_opt_init, eps_opt_step, read_opt_state,
+                       Coarse, eps_coarse_workspace_size, eps_forward_coarse, eps_vjp_coarse,
+                       eps_vjp_real_coarse)
 
 __all__ = [
     "BatchedVjp", "eps_batched_workspace_size", "eps_forward_batched",
@@ -29,6 +31,8 @@ __all__ = [
     "CLOSE_THEN_OPEN", "EPS_MORPH_DILATE", "EPS_MORPH_ERODE", "Morph", "eps_forward_morph",
     "eps_morph_workspace_size", "eps_vjp_morph", "eps_vjp_real_morph", "PreparedVjpMorph",
     "OptParams", "eps_opt_init", "eps_opt_step", "read_opt_state",
+    "Coarse", "eps_coarse_workspace_size", "eps_forward_coarse", "eps_vjp_coarse",
+    "eps_vjp_real_coarse",
 ]
 
 from . import autograd  # noqa: E402  (torch.autograd wrappers)

@@ -123,6 +123,15 @@ _PROTOS = {
     "eps_vjp_real_morph": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP,
                                           ctypes.c_size_t, _VP]),
     "eps_opt_init": (ctypes.c_int, [_VP, _VP, _VP]),
+    "eps_coarse_workspace_size": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+    "eps_forward_coarse": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP,
+                                          ctypes.c_size_t, _VP]),
+    "eps_vjp_coarse": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, ctypes.c_int32,
+                                      ctypes.c_int32, _VP, _VP, _VP, ctypes.c_float, _VP, _VP, _VP,
+                                      ctypes.c_size_t, _VP]),
+    "eps_vjp_real_coarse": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP,
+                                           ctypes.c_size_t, _VP]),
     "eps_opt_step": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP, _VP,
                                     _VP, _VP, ctypes.c_size_t, _VP]),
 }
@@ -640,3 +649,100 @@ def eps_opt_step(prob: Problem, opt: OptParams, state, C, G, M, V, ws, morph=Non
     _check(lib().eps_opt_step(ctypes.byref(p), ctypes.byref(m) if m is not None else None,
                               ctypes.byref(o), _ptr(state), _ptr(C), _ptr(G), _ptr(M), _ptr(V),
                               _ptr(ws), ws.numel(), _stream(stream)), "eps_opt_step")
+
+
+# ------------------------------------------------------ coarse control grid
+
+class eps_coarse_t(ctypes.Structure):
+    _fields_ = [("ncx", ctypes.c_int32), ("ncy", ctypes.c_int32)]
+
+
+@dataclass(frozen=True)
+class Coarse:
+    """Node grid of the coarse control variables (Eq. 2): ncx x ncy nodes
+    spanning the design region edge to edge, hat basis."""
+
+    ncx: int
+    ncy: int
+
+    def c_struct(self) -> eps_coarse_t:
+        g = eps_coarse_t()
+        g.ncx, g.ncy = self.ncx, self.ncy
+        return g
+
+
+def eps_coarse_workspace_size(prob: Problem, coarse: Coarse, n_lambda: int = 1) -> int:
+    n = ctypes.c_size_t(0)
+    p, g = prob.c_struct(), coarse.c_struct()
+    _check(lib().eps_coarse_workspace_size(ctypes.byref(p), ctypes.byref(g), n_lambda,
+                                           ctypes.byref(n)), "eps_coarse_workspace_size")
+    return n.value
+
+
+def _coarse_ws(prob, coarse, ws, device):
+    import torch
+    if ws is None:
+        ws = torch.empty(max(eps_coarse_workspace_size(prob, coarse), 1), dtype=torch.uint8,
+                         device=device)
+    return ws
+
+
+def eps_forward_coarse(prob: Problem, coarse: Coarse, c, eps=None, ws=None, stream=None):
+    """eps_hat [3, nx, ny, nz] from node values c [ncx, ncy]."""
+    import torch
+    _need(c, (coarse.ncx, coarse.ncy), torch.float32, "c")
+    shape = (3, prob.nx, prob.ny, prob.nz)
+    if eps is None:
+        eps = torch.empty(shape, dtype=torch.float32, device=c.device)
+    _need(eps, shape, torch.float32, "eps")
+    if prob.flags & EPS_FLAG_OFFDIAG:
+        raise ValueError("use the C entry point for the off-diagonal term with coarse controls")
+    ws = _coarse_ws(prob, coarse, ws, c.device)
+    p, g = prob.c_struct(), coarse.c_struct()
+    _check(lib().eps_forward_coarse(ctypes.byref(p), ctypes.byref(g), _ptr(c), _ptr(eps), None,
+                                    _ptr(ws), ws.numel(), _stream(stream)), "eps_forward_coarse")
+    return eps
+
+
+def eps_vjp_coarse(prob: Problem, coarse: Coarse, c, EF, EA, scale: float = -2.0, dJdc=None,
+                   eps_out=None, ws=None, stream=None):
+    """Eq. 1 with respect to the node values (complex64 fields).  Returns
+    dJdc [ncx, ncy], or (dJdc, eps_out) when eps_out is given (True allocates)."""
+    import torch
+    _need(c, (coarse.ncx, coarse.ncy), torch.float32, "c")
+    nl = len(EF)
+    if len(EA) != nl or nl > EPS_MAX_LAMBDA:
+        raise ValueError("EF and EA must list the same number (<= 16) of wavelengths")
+    for l in range(nl):
+        _need(EF[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EF[{l}]")
+        _need(EA[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EA[{l}]")
+    if dJdc is None:
+        dJdc = torch.empty((coarse.ncx, coarse.ncy), dtype=torch.float32, device=c.device)
+    _need(dJdc, (coarse.ncx, coarse.ncy), torch.float32, "dJdc")
+    ret_eps = eps_out is not None and eps_out is not False
+    if eps_out is True:
+        eps_out = torch.empty((3, prob.nx, prob.ny, prob.nz), dtype=torch.float32, device=c.device)
+    if ret_eps:
+        _need(eps_out, (3, prob.nx, prob.ny, prob.nz), torch.float32, "eps_out")
+    ws = _coarse_ws(prob, coarse, ws, c.device)
+    ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
+    ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
+    p, g = prob.c_struct(), coarse.c_struct()
+    _check(lib().eps_vjp_coarse(ctypes.byref(p), ctypes.byref(g), _ptr(c), nl, EPS_FIELD_C64, ef, ea,
+                                None, float(scale), _ptr(dJdc), _ptr(eps_out) if ret_eps else None,
+                                _ptr(ws), ws.numel(), _stream(stream)), "eps_vjp_coarse")
+    return (dJdc, eps_out) if ret_eps else dJdc
+
+
+def eps_vjp_real_coarse(prob: Problem, coarse: Coarse, c, G, dJdc=None, ws=None, stream=None):
+    import torch
+    _need(c, (coarse.ncx, coarse.ncy), torch.float32, "c")
+    _need(G, (3, prob.nx, prob.ny, prob.nz), torch.float32, "G")
+    if dJdc is None:
+        dJdc = torch.empty((coarse.ncx, coarse.ncy), dtype=torch.float32, device=c.device)
+    _need(dJdc, (coarse.ncx, coarse.ncy), torch.float32, "dJdc")
+    ws = _coarse_ws(prob, coarse, ws, c.device)
+    p, g = prob.c_struct(), coarse.c_struct()
+    _check(lib().eps_vjp_real_coarse(ctypes.byref(p), ctypes.byref(g), _ptr(c), _ptr(G), _ptr(dJdc),
+                                     _ptr(ws), ws.numel(), _stream(stream)), "eps_vjp_real_coarse")
+    return dJdc

@@ -252,3 +252,24 @@ def test_bad_optimiser_parameters_are_rejected_on_host(L):
                           fake, fake, fake, fake, fake, 1 << 30, None) == 1
     assert L.eps_opt_step(ctypes.byref(p.c_struct()), None, ctypes.byref(o), fake,
                           ctypes.c_void_p(0x10004), fake, fake, fake, fake, 1 << 30, None) == 1
+
+
+# ------------------------------------------------------- coarse control grid
+
+def test_coarse_workspace_and_validation(L):
+    p = prob(mx=420, my=420, nz=24)
+    al = lambda b: (b + 255) // 256 * 256
+    base = ec.eps_workspace_size(p)
+    assert ec.eps_coarse_workspace_size(p, ec.Coarse(36, 36)) == 2 * al(420 * 420 * 4) + base
+    n = ctypes.c_size_t()
+    P = ctypes.byref(p.c_struct())
+    assert L.eps_coarse_workspace_size(P, ctypes.byref(ec.Coarse(1, 36).c_struct()), 1,
+                                       ctypes.byref(n)) == 2
+    assert L.eps_coarse_workspace_size(P, None, 1, ctypes.byref(n)) == 1
+    fake = ctypes.c_void_p(0x10000)
+    G = ctypes.byref(ec.Coarse(36, 36).c_struct())
+    assert L.eps_forward_coarse(P, G, None, fake, None, fake, 1 << 30, None) == 1
+    assert L.eps_forward_coarse(P, G, fake, fake, None, fake, 64, None) == 3
+    arr = (ctypes.c_void_p * 1)(fake)
+    assert L.eps_vjp_coarse(P, G, fake, 1, 0, arr, arr, None, -2.0, fake, None, fake, 64, None) == 3
+    assert L.eps_vjp_real_coarse(P, G, fake, None, fake, fake, 1 << 30, None) == 1
