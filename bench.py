@@ -455,7 +455,8 @@ def _window_error(w, C, EF, EA, g_gpu, half=48):
     return worst
 
 
-def run_variants(torch, ec, synth, dev, flush_l2, sel=("cfg3", "cfg4", "cfg5", "morph")):
+def run_variants(torch, ec, synth, dev, flush_l2,
+                 sel=("cfg3", "cfg4", "cfg5", "morph", "opt", "coarse")):
     """The differentiation (cfg3), batching (cfg4) and precision (cfg5) forms,
     each timed like the main workload (L2 flushed before every call)."""
     out = {}
@@ -548,6 +549,55 @@ def run_variants(torch, ec, synth, dev, flush_l2, sel=("cfg3", "cfg4", "cfg5", "
     if "coarse" in sel:
         out["coarse_controls"] = run_coarse_variant(torch, ec, synth, dev, flush_l2)
     return out
+
+
+def run_morph_variant(torch, ec, synth, dev, flush_l2):
+    """cfg2 with morphological filtering (Eq. 3-6): closing then opening,
+    alpha = 20 (App. B), disks of diameter 40 nm and 150 nm (radius 2 and
+    7.5 subpixels at 10 nm).  The fused call is timed like the main
+    workload; each map kernel is timed with the library's per-kernel events
+    in a separate loop; the r = 2 result is checked against the FP64
+    oracle on the full problem."""
+    import numpy as np
+    from oracle import epschain_oracle as orc
+    from oracle import morph_oracle as mo
+    w = synth.WORKLOADS[2]
+    p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+    Ch = synth.controls(w)
+    C = torch.from_numpy(Ch).to(dev)
+    EFh, EAh = synth.fields(w)
+    EF = [torch.from_numpy(e).to(dev) for e in EFh]
+    EA = [torch.from_numpy(e).to(dev) for e in EAh]
+    G = torch.empty((w.mx, w.my), device=dev)
+    E = torch.empty((3, w.nx, w.ny, w.nz), device=dev)
+    base = ec.PreparedVjp(p, C, EF, EA, G, eps_out=E)
+    ms_base = _timed(base, flush_l2, 50, torch)
+    res = {"workload": w.name, "unit": UNIT, "alpha": 20.0, "ops": "dilate, erode, erode, dilate",
+           "base_chain_ms_per_call": round(ms_base, 4)}
+    for mr in (2.0, 7.5):
+        m = ec.Morph(alpha=20.0, radius=mr)
+        call = ec.PreparedVjpMorph(p, m, C, EF, EA, G, eps_out=E)
+        ms = _timed(call, flush_l2, 50, torch)
+        torch.cuda.synchronize()
+        ec.eps_profile_start()
+        for _ in range(20):
+            flush_l2()
+            call()
+        prof = ec.eps_profile_stop()
+        ec.eps_sync_status()
+        kern = {k: round(v[1] / v[0] * 1e3, 2) for k, v in prof.items()}
+        entry = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
+                 "kernel_us_avg": kern}
+        if mr == 2.0:
+            om = mo.Morph(alpha=20.0, radius=mr)
+            o = orc.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+            ref = mo.vjp_fields_morph(o, om, Ch, EFh, EAh)
+            ref_e = mo.eps_hat_morph(o, om, Ch)
+            g, e = G.cpu().numpy(), E.cpu().numpy()
+            entry["dJdC_max_err_vs_fp64_oracle"] = float(np.max(np.abs(g - ref)) / np.max(np.abs(ref)))
+            entry["eps_max_rel_err_vs_fp64_oracle"] = float(np.max(np.abs(e - ref_e) / ref_e))
+        res[f"disk_radius_{mr:g}"] = entry
+    return res
 
 
 def run_coarse_variant(torch, ec, synth, dev, flush_l2):

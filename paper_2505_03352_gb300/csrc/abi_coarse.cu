@@ -71,8 +71,7 @@ eps_status_t run_transpose(const eps_problem_t *prob, const eps_coarse_t *cg, co
   CoarseArgs a = args_of(prob, cg);
   a.g = g;
   a.dc = dc;
-  const long nodes = (long)cg->ncx * cg->ncy;
-  const long blocks = (nodes + NTHREADS / 32 - 1) / (NTHREADS / 32);
+  const long blocks = (long)cg->ncx * cg->ncy;   // one block per node
   if (blocks > 0x7fffffffL) return EPS_ERR_SHAPE;
   return epsc_host::launch_kernel("eps_coarse_transpose", (const void *)&coarse_transpose_kernel,
                                   dim3((unsigned)blocks), 0, &a, s, true);

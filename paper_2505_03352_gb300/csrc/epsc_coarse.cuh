@@ -7,8 +7,8 @@
 // With the hat basis each subpixel sees the two nodes around it per axis:
 // i0 = floor(x_a / h_x) (clamped to ncx - 2) and i0 + 1 with weights 1 - t
 // and t, t = x_a / h_x - i0.  The transpose gives each node the weighted
-// sum of the subpixel gradient over its support, |x_a - X_i| < h_x: one warp
-// per node, lanes along y, a fixed-order warp reduction (deterministic).
+// sum of the subpixel gradient over its support, |x_a - X_i| < h_x: one block
+// per node, fixed-order reductions (deterministic).
 #pragma once
 
 #include "epsc_common.cuh"
@@ -59,13 +59,14 @@ __global__ void __launch_bounds__(NTHREADS) coarse_expand_kernel(const __grid_co
   }
 }
 
-// one warp per node
+// one block per node: warp w takes rows a_lo + w, a_lo + w + 8, ..., lanes
+// take columns; per-lane, per-warp and per-block sums in a fixed order
 __global__ void __launch_bounds__(NTHREADS) coarse_transpose_kernel(const __grid_constant__ CoarseArgs a) {
+  __shared__ float s_part[NTHREADS / 32];
   griddep_launch_dependents();
   griddep_wait();
-  const int lane = threadIdx.x & 31;
-  const long node = (long)blockIdx.x * (NTHREADS / 32) + (threadIdx.x >> 5);
-  if (node >= (long)a.ncx * a.ncy) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long node = blockIdx.x;
   const int i = (int)(node / a.ncy), j = (int)(node - (long)i * a.ncy);
   // subpixels whose centre lies within one spacing of the node:
   // |(2a + 1)(nc - 1) - 2 i m| < 2m
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(NTHREADS) coarse_transpose_kernel(const __grid
   const int b_lo = max(0, (int)((2L * j * a.my - dy) / (2L * (a.ncy - 1))) - 1);
   const int b_hi = min(a.my - 1, (int)((2L * j * a.my + dy) / (2L * (a.ncy - 1))) + 1);
   float acc = 0.f;
-  for (int xa = a_lo; xa <= a_hi; ++xa) {
+  for (int xa = a_lo + warp; xa <= a_hi; xa += NTHREADS / 32) {
     const float wx = hat_w(xa, i, a.mx, a.ncx);
     if (wx == 0.f) continue;
     const float *row = a.g + (size_t)xa * a.my;
@@ -85,7 +86,13 @@ __global__ void __launch_bounds__(NTHREADS) coarse_transpose_kernel(const __grid
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if (lane == 0) a.dc[node] = acc;
+  if (lane == 0) s_part[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < NTHREADS / 32; ++w) t += s_part[w];
+    a.dc[node] = t;
+  }
 }
 
 }  // namespace epsc
