@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=40)
-    ap.add_argument("--variant-set", default="cfg3,cfg4,cfg5,morph,opt,coarse",
-                    help="comma-separated variants to run (cfg3, cfg4, cfg5, morph, opt, coarse)")
+    ap.add_argument("--variant-set", default="cfg3,cfg4,cfg5,morph,opt,coarse,normals3d",
+                    help="comma-separated variants to run "
+                         "(cfg3, cfg4, cfg5, morph, opt, coarse, normals3d)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the cfg3 / batched cfg4 / reduced-precision cfg5 measurements")
     return ap.parse_args()
@@ -456,7 +457,7 @@ def _window_error(w, C, EF, EA, g_gpu, half=48):
 
 
 def run_variants(torch, ec, synth, dev, flush_l2,
-                 sel=("cfg3", "cfg4", "cfg5", "morph", "opt", "coarse")):
+                 sel=("cfg3", "cfg4", "cfg5", "morph", "opt", "coarse", "normals3d")):
     """The differentiation (cfg3), batching (cfg4) and precision (cfg5) forms,
     each timed like the main workload (L2 flushed before every call)."""
     out = {}
@@ -548,6 +549,43 @@ def run_variants(torch, ec, synth, dev, flush_l2,
         out["optimizer_step"] = run_opt_variant(torch, ec, synth, dev, flush_l2)
     if "coarse" in sel:
         out["coarse_controls"] = run_coarse_variant(torch, ec, synth, dev, flush_l2)
+    if "normals3d" in sel:
+        out["forward_tensor_cfg2"] = run_tensor_variant(torch, ec, synth, dev, flush_l2)
+    return out
+
+
+def run_tensor_variant(torch, ec, synth, dev, flush_l2):
+    """cfg2 forward only: eps_hat alone, with the xy off-diagonal maps, and
+    with 3-D face normals and the full off-diagonal output (4 maps).  The
+    forward writes 12 nz B of eps_hat per column plus 4 nz B per
+    off-diagonal map: an HBM-write-bound stencil."""
+    import ctypes
+    w = synth.WORKLOADS[2]
+    C = torch.from_numpy(synth.controls(w)).to(dev)
+    peak, _ = measured_peaks()
+    cols = w.nx * w.ny
+    eps = torch.empty((3, w.nx, w.ny, w.nz), device=dev)
+    od = torch.empty((4, w.nx, w.ny, w.nz), device=dev)
+    out = {"workload": w.name}
+    for name, flags, n_od in (("eps_hat", 0, 0), ("eps_hat+xy", ec.EPS_FLAG_OFFDIAG, 2),
+                              ("eps_hat+3d_normals+4_offdiag",
+                               ec.EPS_FLAG_OFFDIAG | ec.EPS_FLAG_NORMALS_3D, 4)):
+        p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta, flags=flags)
+        pc = p.c_struct()
+        fn = ec.lib().eps_forward
+        args = (ctypes.byref(pc), ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(eps.data_ptr()),
+                ctypes.c_void_p(od.data_ptr()) if n_od else None)
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+        def call():
+            fn(*args, stream)
+
+        ms = _timed(call, flush_l2, 100, torch)
+        alg = cols * (16 + 4 * w.nz * (3 + n_od))
+        gbs = alg / (ms * 1e-3) / 1e9
+        out[name] = {"us_per_call": round(ms * 1e3, 2), "algorithmic_bytes": alg,
+                     "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
+    ec.eps_sync_status()
     return out
 
 

@@ -63,6 +63,7 @@ typedef enum {
 
 /* flags */
 #define EPS_FLAG_OFFDIAG 1  /* eps_forward also writes the xy inverse-permittivity term */
+#define EPS_FLAG_NORMALS_3D 2 /* 3-D normals at the slab faces (forward only; see eps_forward) */
 
 #define EPS_MAX_LAMBDA 16    /* wavelengths per eps_vjp call */
 #define EPS_MAX_BATCH 64     /* regions per batched call */
@@ -112,6 +113,18 @@ eps_status_t eps_workspace_size(const eps_problem_t *prob, int32_t n_lambda, siz
  *            flags has EPS_FLAG_OFFDIAG: n_x n_y (<1/eps> - 1/<eps>) at the
  *            Ex points (index 0) and Ey points (index 1) on the slab planes,
  *            0 elsewhere.  Forward only: Eq. 1 uses zero off-diagonals.
+ * EPS_FLAG_NORMALS_3D (forward only; eps_vjp* and the batched calls return
+ * EPS_ERR_UNSUPPORTED with it): the Ez cells of the two face planes k0 and
+ * k0 + nk, half slab and half cladding, take Eq. 7 in tensor form with a
+ * 3-D normal, eps^-1 = n n^T <eps^-1> + (I - n n^T) / <eps>, where
+ * <eps> = (A_z + eps_clad)/2, <eps^-1> = (H_z + 1/eps_clad)/2 and n is the
+ * normalised Sobel-consistent gradient of the cell-averaged 3-D density
+ * (g_x, g_y = half the Sobel of U_z, g_z = +4 U_z at k0 and -4 U_z at
+ * k0 + nk; n = z where |g|^2 <= 1e-12).  eps_zz on the face planes becomes
+ * 1 / (eps^-1)_zz; with EPS_FLAG_OFFDIAG as well, offdiag is [4][nx][ny][nz]
+ * and indices 2 and 3 hold (eps^-1)_zx and (eps^-1)_zy at the Ez points
+ * (non-zero on the face planes only).  The xz and yz terms at the Ex and Ey
+ * points vanish in this geometry (their dual cells do not cross a face).
  */
 eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps,
                          float *offdiag, eps_stream_t stream);

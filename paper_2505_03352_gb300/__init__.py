@@ -8,7 +8,7 @@ wraps it as torch.autograd.Functions, `synth` draws the seeded inputs.
 
 from .epschain import (BatchedVjp, eps_batched_workspace_size, eps_forward_batched,
                        EPS_BC_CLAMP, EPS_BC_PERIODIC, EPS_FIELD_C64, EPS_FIELD_BF16X2_SCALED,
-                       EPS_FIELD_F16X2_SCALED, EPS_FLAG_OFFDIAG, EpsError, PreparedVjp, Problem,
+                       EPS_FIELD_F16X2_SCALED, EPS_FLAG_OFFDIAG, EPS_FLAG_NORMALS_3D, EpsError, PreparedVjp, Problem,
                        eps_field_pack, eps_forward, eps_packed_field_bytes,
                        eps_profile_start, eps_profile_stop, eps_set_l2_fetch_granularity,
                        eps_status_string, eps_sync_status,
@@ -23,7 +23,7 @@ from .epschain import (BatchedVjp, eps_batched_workspace_size, eps_forward_batch
 __all__ = [
     "BatchedVjp", "eps_batched_workspace_size", "eps_forward_batched",
     "EPS_BC_CLAMP", "EPS_BC_PERIODIC", "EPS_FIELD_C64", "EPS_FIELD_BF16X2_SCALED",
-    "EPS_FIELD_F16X2_SCALED", "EPS_FLAG_OFFDIAG", "EpsError", "PreparedVjp", "Problem", "eps_forward",
+    "EPS_FIELD_F16X2_SCALED", "EPS_FLAG_OFFDIAG", "EPS_FLAG_NORMALS_3D", "EpsError", "PreparedVjp", "Problem", "eps_forward",
     "eps_field_pack", "eps_packed_field_bytes",
     "eps_profile_start", "eps_profile_stop", "eps_set_l2_fetch_granularity", "eps_status_string",
     "eps_sync_status", "eps_vjp",

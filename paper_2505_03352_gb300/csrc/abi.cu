@@ -28,6 +28,7 @@ namespace {
 
 struct Resolved {
   bool empty;
+  bool normals3d;   // EPS_FLAG_NORMALS_3D: forward only
   Geometry g;
   int rp1;
   float w[MAX_BOX * MAX_BOX];
@@ -40,7 +41,7 @@ eps_status_t resolve(const eps_problem_t *p, Resolved *r) {
   std::memset(r, 0, sizeof(*r));
   if (p->sub != 2) return EPS_ERR_UNSUPPORTED;
   if (p->bc != EPS_BC_CLAMP && p->bc != EPS_BC_PERIODIC) return EPS_ERR_INVALID_ARG;
-  if (p->flags & ~EPS_FLAG_OFFDIAG) return EPS_ERR_INVALID_ARG;
+  if (p->flags & ~(EPS_FLAG_OFFDIAG | EPS_FLAG_NORMALS_3D)) return EPS_ERR_INVALID_ARG;
   if (!std::isfinite(p->radius) || !(p->radius > 0.f)) return EPS_ERR_INVALID_ARG;
   if (!std::isfinite(p->beta) || !std::isfinite(p->eta)) return EPS_ERR_INVALID_ARG;
   if (!std::isfinite(p->eps_core) || !std::isfinite(p->eps_clad) || !(p->eps_core > 0.f) ||
@@ -54,6 +55,7 @@ eps_status_t resolve(const eps_problem_t *p, Resolved *r) {
   if (k0 < 0 || k0 + p->slab_nk > p->nz - 1) return EPS_ERR_SHAPE;
 
   r->empty = p->mx == 0 || p->my == 0;
+  r->normals3d = (p->flags & EPS_FLAG_NORMALS_3D) != 0;
   Geometry &g = r->g;
   g.mx = p->mx;
   g.my = p->my;
@@ -431,6 +433,7 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps, 
   fa.r.mode = MODE_FWD;
   fa.r.write_eps = 1;
   fa.r.write_offdiag = od ? 1 : 0;
+  fa.r.normals3d = (prob->flags & EPS_FLAG_NORMALS_3D) ? 1 : 0;
   fa.r.eps = eps;
   fa.r.offdiag = od ? offdiag : nullptr;
   const KernelEntry k = fwd_entry(r.rp1, r.g.bc);
@@ -449,6 +452,7 @@ eps_status_t vjp_args(const Resolved &r, const float *C, int32_t n_lambda, int32
                       float scale, const float *dJdC, const float *eps_out, const void *ws,
                       size_t ws_bytes, bool *skip) {
   *skip = false;
+  if (r.normals3d) return EPS_ERR_UNSUPPORTED;   // forward only
   if (n_lambda < 0 || n_lambda > EPS_MAX_LAMBDA) return EPS_ERR_INVALID_ARG;
   if (field_type != EPS_FIELD_C64 && field_type != EPS_FIELD_BF16X2_SCALED &&
       field_type != EPS_FIELD_F16X2_SCALED)
@@ -554,6 +558,7 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
   Resolved r;
   eps_status_t st = resolve(prob, &r);
   if (st != EPS_OK) return st;
+  if (r.normals3d) return EPS_ERR_UNSUPPORTED;   // forward only
   if (r.empty) return EPS_OK;
   if (!C || !G || !dJdC) return EPS_ERR_INVALID_ARG;
   if (!aligned(C, 4) || !aligned(G, 4) || !aligned(dJdC, 4)) return EPS_ERR_INVALID_ARG;
@@ -731,6 +736,7 @@ eps_status_t resolve_batch(int32_t n, const eps_problem_t *probs, std::vector<Re
   for (int k = 0; k < n; ++k) {
     eps_status_t st = resolve(&probs[k], &rs[k]);
     if (st != EPS_OK) return st;
+    if (rs[k].normals3d) return EPS_ERR_UNSUPPORTED;   // single-region forward only
     ws_off[k] = off;
     off += rs[k].empty ? 0 : workspace_bytes(rs[k].g);
   }

@@ -139,6 +139,7 @@ eps_status_t eps_vjp_real_coarse(const eps_problem_t *prob, const eps_coarse_t *
   CoarsePlan P;
   eps_status_t st = plan(prob, coarse, &P);
   if (st != EPS_OK) return st;
+  if (prob->flags & EPS_FLAG_NORMALS_3D) return EPS_ERR_UNSUPPORTED;   // forward only
   if (P.empty) return EPS_OK;
   if (!c || !G || !dJdc) return EPS_ERR_INVALID_ARG;
   if (!aligned(c, 4) || !aligned(G, 4) || !aligned(dJdc, 4)) return EPS_ERR_INVALID_ARG;

@@ -210,6 +210,7 @@ eps_status_t eps_vjp_real_morph(const eps_problem_t *prob, const eps_morph_t *mo
   MorphPlan P;
   eps_status_t st = plan(prob, morph, &P);
   if (st != EPS_OK) return st;
+  if (prob->flags & EPS_FLAG_NORMALS_3D) return EPS_ERR_UNSUPPORTED;   // forward only
   if (P.empty) return EPS_OK;
   if (!C || !G || !dJdC) return EPS_ERR_INVALID_ARG;
   if (!aligned(C, 4) || !aligned(G, 4) || !aligned(dJdC, 4)) return EPS_ERR_INVALID_ARG;

@@ -60,6 +60,7 @@ struct FwdRegion {
   int mode;
   int write_eps;
   int write_offdiag;
+  int normals3d;                 // 3-D normals at the slab faces (forward only)
   int stage_floats;              // shared floats available for eps_hat staging
   const float *C;
   float *eps;

@@ -34,18 +34,22 @@ struct FwdSmem {
   static constexpr int OFF_IE = OFF_E + UA * UB;
   static constexpr int OFF_UX = OFF_IE + UA * UB;
   static constexpr int OFF_UY = OFF_UX + HN;
-  static constexpr int TOTAL = OFF_UY + HN;
+  static constexpr int OFF_UZ = OFF_UY + HN;       // U_z with halo (3-D face normals)
+  static constexpr int TOTAL = OFF_UZ + HN;
   static constexpr size_t BYTES = sizeof(float) * TOTAL;
   // dynamic shared memory of a launch: max(BYTES, the eps_hat staging area)
 };
 
 // Value of output component `comp` on plane k: comp 0/1 = eps_xx/yy and
 // 3/4 = off-diagonal at the Ex/Ey points take `vmain` on the slab planes;
-// comp 2 = eps_zz takes vzi inside the slab and vzf on the two face planes.
+// comp 2 = eps_zz takes vzi inside the slab and vzf on the two face planes;
+// comp 5/6 = eta_zx/zy at the Ez points take vmain on the lower face plane,
+// -vmain on the upper one and 0 elsewhere.
 __device__ __forceinline__ float plane_value(int comp, int k, int k0, int nk, float vmain,
                                              float vzi, float vzf, float clad) {
   const bool slab = k >= k0 + 1 && k <= k0 + nk;
   if (comp < 2) return slab ? vmain : clad;
+  if (comp > 4) return k == k0 ? vmain : (k == k0 + nk ? -vmain : 0.f);
   if (comp > 2) return slab ? vmain : 0.f;
   if (k >= k0 + 1 && k <= k0 + nk - 1) return vzi;
   if (k == k0 || k == k0 + nk) return vzf;
@@ -72,6 +76,7 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
   float *sie = smem + S::OFF_IE;
   float *sUx = smem + S::OFF_UX;
   float *sUy = smem + S::OFF_UY;
+  float *sUz = smem + S::OFF_UZ;
 
   const Geometry &g = rg.g;
   const int tid = threadIdx.x;
@@ -166,6 +171,10 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
                         (su[(ra + 1) * UB + rb - 1] + su[(ra + 1) * UB + rb]));
     sUy[idx] = 0.25f * ((su[(ra - 1) * UB + rb] + su[(ra - 1) * UB + rb + 1]) +
                         (su[ra * UB + rb] + su[ra * UB + rb + 1]));
+    // Omega_z: a in {2i-1, 2i}, b in {2j-1, 2j}
+    if (rg.normals3d)
+      sUz[idx] = 0.25f * ((su[(ra - 1) * UB + rb - 1] + su[(ra - 1) * UB + rb]) +
+                          (su[ra * UB + rb - 1] + su[ra * UB + rb]));
   }
 
   const int cr = tid / TJ, cc = tid - (tid / TJ) * TJ;
@@ -216,6 +225,36 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
   const float odx = gxx * gyx * ig2x * (Hx - iAx);
   const float ody = gxy * gyy * ig2y * (Hy - iAy);
 
+  // 3-D normals at the slab faces (forward only).  The Ez cells of planes
+  // k0 and k0 + nk are half slab, half cladding.  Sobel-consistent central
+  // differences of the cell-averaged density: in plane half the Sobel of
+  // U_z, along z +4 U_z at the lower face and -4 U_z at the upper face.
+  // Row z of eps^-1 = n n^T <eps^-1> + (I - n n^T) / <eps> with
+  // <eps> = (A_z + eps_clad)/2, <eps^-1> = (H_z + 1/eps_clad)/2; without a
+  // defined normal the base rule n = z stays.  ezf3 is eps_zz on both face
+  // planes; ezx3, ezy3 are eta_zx, eta_zy on the lower face (negated on the
+  // upper one).
+  float ezf3 = ezf, ezx3 = 0.f, ezy3 = 0.f;
+  if (rg.normals3d) {
+    constexpr int P = S::HP;
+    const int h = (cr + 1) * P + (cc + 1);
+    const float gx = 0.5f * ((sUz[h + P - 1] - sUz[h - P - 1]) + 2.f * (sUz[h + P] - sUz[h - P]) +
+                             (sUz[h + P + 1] - sUz[h - P + 1]));
+    const float gy = 0.5f * ((sUz[h - P + 1] - sUz[h - P - 1]) + 2.f * (sUz[h + 1] - sUz[h - 1]) +
+                             (sUz[h + P + 1] - sUz[h + P - 1]));
+    const float gz = 4.f * sUz[h];
+    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    if (g2 > NORMAL_TAU2) {
+      const float ig = __frcp_rn(g2);
+      const float a_inv = fmaf(0.5f, Hz, 0.5f / g.eps_clad);
+      const float b = __frcp_rn(fmaf(0.5f, Az, 0.5f * g.eps_clad));
+      const float nz2 = gz * gz * ig;
+      ezf3 = __frcp_rn(fmaf(nz2, a_inv, (1.f - nz2) * b));
+      ezx3 = gz * gx * ig * (a_inv - b);
+      ezy3 = gz * gy * ig * (a_inv - b);
+    }
+  }
+
   // ---- eps_hat store: whole-tile staging + bulk (TMA) stores ------------
   // Each thread writes its column's planes of `ncomp` components into shared
   // memory (rows of TJ * nz floats per component and tile row), then one
@@ -227,7 +266,7 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
   bool bulk_pending = false;
   if (rg.write_eps || rg.write_offdiag) {
     const int c_first = rg.write_eps ? 0 : 3;
-    const int c_last = rg.write_offdiag ? 4 : 2;
+    const int c_last = rg.write_offdiag ? (rg.normals3d ? 6 : 4) : 2;
     const size_t cplane = (size_t)g.nx * g.ny * g.nz;
     const int comp_floats = TI * TJ * g.nz;
     const int per_round = rg.stage_floats / comp_floats;
@@ -243,6 +282,21 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
         }
         if (cr < nvi && cc < nvj) {
           for (int comp = c0; comp <= c1; ++comp) {
+            if (comp > 4) {
+              // eta_zx / eta_zy: the two face planes only
+              const float v = comp == 5 ? ezx3 : ezy3;
+              float4 *dz = reinterpret_cast<float4 *>(sbuf + (comp - c0) * comp_floats +
+                                                      (cr * TJ + cc) * g.nz);
+              const int f0 = g.k0, f1 = g.k0 + g.nk;
+              for (int k4 = 0; k4 < nz4; ++k4) {
+                const int k = 4 * k4;
+                float t[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) t[q] = k + q == f0 ? v : (k + q == f1 ? -v : 0.f);
+                dz[k4] = make_float4(t[0], t[1], t[2], t[3]);
+              }
+              continue;
+            }
             const float vin = comp == 0 ? ex : comp == 1 ? ey : comp == 2 ? ezi : comp == 3 ? odx : ody;
             const float out = comp < 3 ? g.eps_clad : 0.f;
             const int zlen = comp == 2 ? g.nk - 1 : g.nk;   // planes k0+1 .. k0+zlen take vin
@@ -269,7 +323,7 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
                   const int kk = k + q;
                   const bool in = kk >= lo && kk <= hi;
                   const bool face = kk == kf0 || kk == kf1;
-                  t[q] = in ? vin : (face ? ezf : out);
+                  t[q] = in ? vin : (face ? ezf3 : out);
                 }
                 dst[k4] = make_float4(t[0], t[1], t[2], t[3]);
               }
@@ -294,10 +348,11 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
       // plane counts not a multiple of 4: thread per column
       for (int comp = c_first; comp <= c_last; ++comp) {
         float *base = comp < 3 ? rg.eps + comp * cplane : rg.offdiag + (comp - 3) * cplane;
-        const float vm = comp == 0 ? ex : comp == 1 ? ey : comp == 3 ? odx : ody;
+        const float vm = comp == 0 ? ex : comp == 1 ? ey : comp == 3 ? odx : comp == 4 ? ody
+                         : comp == 5 ? ezx3 : ezy3;
         float *dst = base + ((size_t)ci * g.ny + cj) * g.nz;
         for (int k = 0; k < g.nz; ++k)
-          dst[k] = plane_value(comp, k, g.k0, g.nk, vm, ezi, ezf, g.eps_clad);
+          dst[k] = plane_value(comp, k, g.k0, g.nk, vm, ezi, ezf3, g.eps_clad);
       }
     }
   }

@@ -25,6 +25,7 @@ STATUS_NAMES = {
 EPS_BC_CLAMP, EPS_BC_PERIODIC = 0, 1
 EPS_FIELD_C64, EPS_FIELD_BF16X2_SCALED, EPS_FIELD_F16X2_SCALED = 0, 1, 2
 EPS_FLAG_OFFDIAG = 1
+EPS_FLAG_NORMALS_3D = 2
 EPS_MAX_LAMBDA = 16
 
 
@@ -206,7 +207,8 @@ def eps_forward(prob: Problem, C, eps=None, offdiag=None, stream=None):
     _need(eps, shape, torch.float32, "eps")
     want_od = bool(prob.flags & EPS_FLAG_OFFDIAG)
     if want_od and offdiag is None:
-        offdiag = torch.empty((2,) + shape[1:], dtype=torch.float32, device=C.device)
+        n_od = 4 if prob.flags & EPS_FLAG_NORMALS_3D else 2
+        offdiag = torch.empty((n_od,) + shape[1:], dtype=torch.float32, device=C.device)
     p = prob.c_struct()
     _check(lib().eps_forward(ctypes.byref(p), _ptr(C), _ptr(eps), _ptr(offdiag) if want_od else None,
                              _stream(stream)), "eps_forward")
