@@ -171,9 +171,9 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
  * [n][n_lambda][2][3].  n_lambda <= EPS_MAX_BATCH_LAMBDA; complex64 fields
  * only; eps_out may be NULL or hold NULL entries.  The workspace is the
  * regions' eps_workspace_size() laid end to end (eps_batched_workspace_size).
- * One contraction launch covers every region; regions that share a filter
- * radius and boundary rule share one stencil and one scatter launch (tiles
- * of the largest regions first).  Results equal the per-region calls'.
+ * One contraction launch covers every region; the stencil and scatter
+ * launches follow the batch's launch shapes (below: by default one launch
+ * each per radius group).  Results equal the per-region calls'.
  */
 eps_status_t eps_batched_workspace_size(int32_t n, const eps_problem_t *probs, int32_t n_lambda,
                                         size_t *bytes);
@@ -184,6 +184,44 @@ eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float 
                              const void *const *EA, const float *field_scales, float scale,
                              float *const *dJdC, float *const *eps_out, void *ws, size_t ws_bytes,
                              eps_stream_t stream);
+
+/*
+ * Launch shapes of the batched calls, and their autotuner.
+ *
+ * eps_vjp_batched runs in one of two launch forms: one persistent
+ * mixed-radius stencil launch and one scatter launch per boundary rule
+ * (`multi` = 1; a batch that holds two different radii of the same radius
+ * class ceil(R) needs one more launch per extra radius), or one stencil
+ * and one scatter launch per (radius, boundary rule) group with one block
+ * per tile (`multi` = 0, the default).  The shapes are: that form, the persistent
+ * stencil and scatter blocks per SM, the contraction's blocks per SM, and
+ * how many eps_hat components are staged per round of bulk stores (1 or
+ * 3; fewer means less shared memory per block).  Results do not depend on
+ * the shapes (every output element is computed the same way).
+ *
+ * eps_autotune_batched takes the arguments of eps_vjp_batched plus `reps`
+ * (1 .. 1000): it runs the batched call with candidate shapes (coordinate
+ * descent, two sweeps, each candidate timed with CUDA events over `reps`
+ * calls after one warm-up call), keeps the fastest, and caches it for this
+ * batch (keyed by n, n_lambda and every eps_problem_t) in the process, where
+ * later eps_vjp_batched calls on the same batch pick it up.  It writes the
+ * same outputs as eps_vjp_batched, synchronises `stream`, and returns
+ * EPS_ERR_UNSUPPORTED while `stream` is capturing (tune first, then
+ * capture).  `result` (host, may be NULL) receives the choice and the mean
+ * milliseconds per call with the default and the chosen shapes.
+ */
+typedef struct {
+  int32_t multi, stencil_blocks_per_sm, scatter_blocks_per_sm, contract_blocks_per_sm;
+  int32_t stage_components, evaluations;
+  float default_ms, tuned_ms;
+} eps_tuning_t;
+
+eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
+                                  int32_t n_lambda, int32_t field_type, const void *const *EF,
+                                  const void *const *EA, const float *field_scales, float scale,
+                                  float *const *dJdC, float *const *eps_out, void *ws,
+                                  size_t ws_bytes, int32_t reps, eps_tuning_t *result,
+                                  eps_stream_t stream);
 
 /*
  * Reduced-precision field storage (BF16 / FP16 complex pairs with one

@@ -18,6 +18,7 @@
 #include "epsc_contract_tma.cuh"
 #include "epsc_pack.cuh"
 #include "epsc_launch.h"
+#include "epsc_multi.cuh"
 
 using namespace epsc;
 
@@ -719,8 +720,59 @@ eps_status_t eps_profile_stop(eps_profile_entry_t *entries, int32_t max_entries,
 
 namespace {
 
-// Regions that share one conic filter and boundary rule run in one batched
-// stencil launch and one batched scatter launch.
+// Launch shapes of a batched call.  Two launch forms:
+//  * multi:   one mixed-radius persistent stencil launch and one scatter
+//             launch per boundary rule (`fwd_bps` / `bwd_bps` blocks per SM
+//             walk the tile list, heaviest radius class first);
+//  * grouped: one stencil and one scatter launch per (radius, boundary
+//             rule) group, one block per tile.
+// eps_autotune_batched times these choices on the caller's batch and caches
+// the fastest per batch signature; other calls use the cache or the default.
+struct BatchTuning {
+  int multi;          // 1: multi form, 0: grouped form
+  int fwd_bps;        // persistent stencil blocks per SM (multi form)
+  int bwd_bps;        // persistent scatter blocks per SM (multi form)
+  int contract_bps;   // batched contraction blocks per SM
+  int stage_comps;    // eps_hat components staged per round of bulk stores (1 or 3)
+};
+// Default: the grouped form, measured faster on the 64-region batch (radius
+// classes 2 .. 8): one kernel holding all twelve radius bodies runs them side
+// by side on an SM and lost to per-class launches there.
+constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 8, 3};
+
+std::mutex g_tune_mu;
+std::vector<std::pair<uint64_t, BatchTuning>> g_tune;   // small: one entry per tuned batch
+
+uint64_t batch_signature(int32_t n, const eps_problem_t *probs, int32_t n_lambda) {
+  uint64_t h = 1469598103934665603ull;   // FNV-1a over the problem structs
+  auto mix = [&](const void *p, size_t bytes) {
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < bytes; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  };
+  mix(&n, sizeof(n));
+  mix(&n_lambda, sizeof(n_lambda));
+  for (int k = 0; k < n; ++k) mix(&probs[k], sizeof(eps_problem_t));
+  return h;
+}
+
+BatchTuning lookup_tuning(uint64_t sig) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto &e : g_tune)
+    if (e.first == sig) return e.second;
+  return DEFAULT_TUNING;
+}
+
+void store_tuning(uint64_t sig, const BatchTuning &t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto &e : g_tune)
+    if (e.first == sig) {
+      e.second = t;
+      return;
+    }
+  g_tune.push_back({sig, t});
+}
+
+// Regions that share one conic filter and boundary rule (grouped form).
 struct Group {
   int rp1, bc;
   float radius;
@@ -744,6 +796,8 @@ eps_status_t resolve_batch(int32_t n, const eps_problem_t *probs, std::vector<Re
   return EPS_OK;
 }
 
+long fwd_tiles(const Resolved &r) { return (long)fwd_grid(r.g).x * fwd_grid(r.g).y; }
+
 std::vector<Group> make_groups(const std::vector<Resolved> &rs, const eps_problem_t *probs) {
   std::vector<Group> gs;
   for (int k = 0; k < (int)rs.size(); ++k) {
@@ -755,15 +809,49 @@ std::vector<Group> make_groups(const std::vector<Resolved> &rs, const eps_proble
     if (gi == gs.size()) gs.push_back(Group{rs[k].rp1, rs[k].g.bc, probs[k].radius, {}});
     gs[gi].regions.push_back(k);
   }
-  auto tiles = [&](int k) { return (long)fwd_grid(rs[k].g).x * fwd_grid(rs[k].g).y; };
   for (Group &g : gs)
     std::stable_sort(g.regions.begin(), g.regions.end(),
-                     [&](int x, int y) { return tiles(x) > tiles(y); });
+                     [&](int x, int y) { return fwd_tiles(rs[x]) > fwd_tiles(rs[y]); });
   return gs;
 }
 
-// One batched stencil launch per group (forward-only or VJP mode).
-eps_status_t run_fwd_batched(const std::vector<Group> &gs, const std::vector<Resolved> &rs,
+// Launch sets of the multi form: one boundary rule, at most one radius per
+// radius class; regions ordered heaviest class first, then largest first.
+struct LaunchSet {
+  int bc;
+  float radius_of[MAX_RP1 + 1];   // radius of each class present, 0 if absent
+  std::vector<int> regions;
+};
+
+std::vector<LaunchSet> make_sets(const std::vector<Resolved> &rs, const eps_problem_t *probs) {
+  std::vector<LaunchSet> sets;
+  for (int k = 0; k < (int)rs.size(); ++k) {
+    if (rs[k].empty) continue;
+    const int c = rs[k].rp1;
+    size_t si = 0;
+    for (; si < sets.size(); ++si)
+      if (sets[si].bc == rs[k].g.bc &&
+          (sets[si].radius_of[c] == 0.f || sets[si].radius_of[c] == probs[k].radius))
+        break;
+    if (si == sets.size()) {
+      LaunchSet ls;
+      ls.bc = rs[k].g.bc;
+      for (float &r : ls.radius_of) r = 0.f;
+      sets.push_back(ls);
+    }
+    sets[si].radius_of[c] = probs[k].radius;
+    sets[si].regions.push_back(k);
+  }
+  for (LaunchSet &ls : sets)
+    std::stable_sort(ls.regions.begin(), ls.regions.end(), [&](int x, int y) {
+      if (rs[x].rp1 != rs[y].rp1) return rs[x].rp1 > rs[y].rp1;
+      return fwd_tiles(rs[x]) > fwd_tiles(rs[y]);
+    });
+  return sets;
+}
+
+// Grouped form: one batched stencil launch per group.
+eps_status_t run_fwd_grouped(const std::vector<Group> &gs, const std::vector<Resolved> &rs,
                              const std::vector<FwdRegion> &regions, int ncomp, int *err,
                              cudaStream_t s, bool pdl) {
   FwdBatchArgs *ba = new FwdBatchArgs;
@@ -795,7 +883,7 @@ eps_status_t run_fwd_batched(const std::vector<Group> &gs, const std::vector<Res
   return st;
 }
 
-eps_status_t run_bwd_batched(const std::vector<Group> &gs, const std::vector<Resolved> &rs,
+eps_status_t run_bwd_grouped(const std::vector<Group> &gs, const std::vector<Resolved> &rs,
                              const std::vector<BwdRegion> &regions, int *err, cudaStream_t s) {
   BwdBatchArgs *ba = new BwdBatchArgs;
   eps_status_t st = EPS_OK;
@@ -822,51 +910,99 @@ eps_status_t run_bwd_batched(const std::vector<Group> &gs, const std::vector<Res
   return st;
 }
 
-}  // namespace
-
-extern "C" {
-
-eps_status_t eps_batched_workspace_size(int32_t n, const eps_problem_t *probs, int32_t n_lambda,
-                                        size_t *bytes) {
-  if (!bytes) return EPS_ERR_INVALID_ARG;
-  if (n_lambda < 0 || n_lambda > EPS_MAX_BATCH_LAMBDA) return EPS_ERR_INVALID_ARG;
-  std::vector<Resolved> rs;
-  std::vector<size_t> off;
-  return resolve_batch(n, probs, rs, off, bytes);
-}
-
-eps_status_t eps_forward_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
-                                 float *const *eps, eps_stream_t stream) {
-  std::vector<Resolved> rs;
-  std::vector<size_t> off;
-  size_t total = 0;
-  eps_status_t st = resolve_batch(n, probs, rs, off, &total);
+// Multi form: one persistent mixed-radius launch per set.
+eps_status_t run_fwd_multi(const std::vector<LaunchSet> &sets, const std::vector<Resolved> &rs,
+                           const std::vector<FwdRegion> &regions, int ncomp, int bps, int *err,
+                           cudaStream_t s, bool pdl) {
+  int nsm = 0;
+  eps_status_t st = sm_count(&nsm);
   if (st != EPS_OK) return st;
-  if (n == 0) return EPS_OK;
-  if (!C || !eps) return EPS_ERR_INVALID_ARG;
-  std::vector<FwdRegion> regions(n);
-  for (int k = 0; k < n; ++k) {
-    if (rs[k].empty) continue;
-    if (probs[k].flags & EPS_FLAG_OFFDIAG) return EPS_ERR_UNSUPPORTED;
-    if (!C[k] || !eps[k] || !aligned(C[k], 4) || !aligned(eps[k], 16)) return EPS_ERR_INVALID_ARG;
-    std::memset(&regions[k], 0, sizeof(FwdRegion));
-    regions[k].g = rs[k].g;
-    regions[k].mode = MODE_FWD;
-    regions[k].write_eps = 1;
-    regions[k].C = C[k];
-    regions[k].eps = eps[k];
+  FwdMultiArgs *ma = new FwdMultiArgs;
+  for (const LaunchSet &ls : sets) {
+    std::memset(ma, 0, sizeof(*ma));
+    ma->n = (int)ls.regions.size();
+    ma->err = err;
+    size_t smem = 0;
+    int tiles = 0;
+    for (int q = 0; q < ma->n; ++q) {
+      const int ri = ls.regions[q];
+      const int c = rs[ri].rp1;
+      std::memcpy(ma->w + woff(c), rs[ri].w, sizeof(float) * (2 * c - 1) * (2 * c - 1));
+      int sf = 0;
+      smem = std::max(smem, fwd_smem(fwd_entry(c, ls.bc), rs[ri].g, ncomp, &sf));
+      const dim3 grid = fwd_grid(rs[ri].g);
+      ma->tile_start[q] = tiles;
+      ma->tiles_j[q] = (int)grid.x;
+      ma->rp1[q] = c;
+      tiles += (int)(grid.x * grid.y);
+      ma->r[q] = regions[ri];
+    }
+    ma->tile_start[ma->n] = tiles;
+    for (int q = 0; q < ma->n; ++q) ma->r[q].stage_floats = (int)(smem / sizeof(float));
+    const long blocks = std::max<long>(1, std::min<long>(tiles, (long)nsm * bps));
+    st = launch("eps_batched_stencil", fwd_multi_entry(ls.bc), dim3((unsigned)blocks), smem, ma, s,
+                pdl);
+    if (st != EPS_OK) break;
   }
-  int *err = nullptr;
-  if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
-  const std::vector<Group> gs = make_groups(rs, probs);
-  return run_fwd_batched(gs, rs, regions, 3, err, (cudaStream_t)stream, false);
+  delete ma;
+  return st;
 }
 
-eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
-                             int32_t n_lambda, int32_t field_type, const void *const *EF,
-                             const void *const *EA, const float *field_scales, float scale,
-                             float *const *dJdC, float *const *eps_out, void *ws, size_t ws_bytes,
-                             eps_stream_t stream) {
+eps_status_t run_bwd_multi(const std::vector<LaunchSet> &sets, const std::vector<Resolved> &rs,
+                           const std::vector<BwdRegion> &regions, int bps, int *err,
+                           cudaStream_t s) {
+  int nsm = 0;
+  eps_status_t st = sm_count(&nsm);
+  if (st != EPS_OK) return st;
+  BwdMultiArgs *ma = new BwdMultiArgs;
+  for (const LaunchSet &ls : sets) {
+    std::memset(ma, 0, sizeof(*ma));
+    ma->n = (int)ls.regions.size();
+    ma->err = err;
+    size_t smem = 0;
+    int tiles = 0;
+    for (int q = 0; q < ma->n; ++q) {
+      const int ri = ls.regions[q];
+      const int c = rs[ri].rp1;
+      std::memcpy(ma->w + woff(c), rs[ri].w, sizeof(float) * (2 * c - 1) * (2 * c - 1));
+      smem = std::max(smem, bwd_entry(c, ls.bc).smem);
+      const dim3 grid = bwd_grid(rs[ri].g);
+      ma->tile_start[q] = tiles;
+      ma->tiles_j[q] = (int)grid.x;
+      ma->rp1[q] = c;
+      tiles += (int)(grid.x * grid.y);
+      ma->r[q] = regions[ri];
+    }
+    ma->tile_start[ma->n] = tiles;
+    const long blocks = std::max<long>(1, std::min<long>(tiles, (long)nsm * bps));
+    st = launch("eps_batched_scatter", bwd_multi_entry(ls.bc), dim3((unsigned)blocks), smem, ma, s,
+                true);
+    if (st != EPS_OK) break;
+  }
+  delete ma;
+  return st;
+}
+
+eps_status_t run_fwd_batch(const std::vector<Resolved> &rs, const eps_problem_t *probs,
+                           const std::vector<FwdRegion> &regions, int ncomp,
+                           const BatchTuning &t, int *err, cudaStream_t s, bool pdl) {
+  const int nc = std::min(ncomp, t.stage_comps);
+  if (t.multi) return run_fwd_multi(make_sets(rs, probs), rs, regions, nc, t.fwd_bps, err, s, pdl);
+  return run_fwd_grouped(make_groups(rs, probs), rs, regions, nc, err, s, pdl);
+}
+
+eps_status_t run_bwd_batch(const std::vector<Resolved> &rs, const eps_problem_t *probs,
+                           const std::vector<BwdRegion> &regions, const BatchTuning &t, int *err,
+                           cudaStream_t s) {
+  if (t.multi) return run_bwd_multi(make_sets(rs, probs), rs, regions, t.bwd_bps, err, s);
+  return run_bwd_grouped(make_groups(rs, probs), rs, regions, err, s);
+}
+
+eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float *const *C,
+                              int32_t n_lambda, int32_t field_type, const void *const *EF,
+                              const void *const *EA, const float *field_scales, float scale,
+                              float *const *dJdC, float *const *eps_out, void *ws, size_t ws_bytes,
+                              cudaStream_t s, const BatchTuning *forced) {
   std::vector<Resolved> rs;
   std::vector<size_t> off;
   size_t total = 0;
@@ -884,6 +1020,7 @@ eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float 
   if (!ws || !aligned(ws, 256) || ws_bytes < total) return EPS_ERR_WORKSPACE;
   int *err = nullptr;
   if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
+  const BatchTuning t = forced ? *forced : lookup_tuning(batch_signature(n, probs, n_lambda));
 
   ContractBatchArgs *ca = new ContractBatchArgs;
   std::memset(ca, 0, sizeof(*ca));
@@ -952,7 +1089,6 @@ eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float 
     br[k].dJdC = dJdC[k];
   }
   ca->ncol = ncol;
-  cudaStream_t s = (cudaStream_t)stream;
   if (ncol > 0) {
     int nsm = 0;
     if ((st = sm_count(&nsm)) != EPS_OK) {
@@ -960,16 +1096,146 @@ eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float 
       return st;
     }
     const long per_block = (NTHREADS / 32) * 4;
-    const long blocks = std::max<long>(1, std::min<long>((ncol + per_block - 1) / per_block, (long)nsm * 8));
+    const long blocks = std::max<long>(
+        1, std::min<long>((ncol + per_block - 1) / per_block, (long)nsm * t.contract_bps));
     st = launch("eps_batched_contract", contract_batched_entry(), dim3((unsigned)blocks), 0, ca, s);
   }
   delete ca;
   if (st != EPS_OK) return st;
-  const std::vector<Group> gs = make_groups(rs, probs);
   bool any_eps = false;
   for (int k = 0; k < n; ++k) any_eps = any_eps || (eps_out && eps_out[k]);
-  if ((st = run_fwd_batched(gs, rs, fr, any_eps ? 3 : 0, err, s, true)) != EPS_OK) return st;
-  return run_bwd_batched(gs, rs, br, err, s);
+  if ((st = run_fwd_batch(rs, probs, fr, any_eps ? 3 : 0, t, err, s, true)) != EPS_OK) return st;
+  return run_bwd_batch(rs, probs, br, t, err, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+eps_status_t eps_batched_workspace_size(int32_t n, const eps_problem_t *probs, int32_t n_lambda,
+                                        size_t *bytes) {
+  if (!bytes) return EPS_ERR_INVALID_ARG;
+  if (n_lambda < 0 || n_lambda > EPS_MAX_BATCH_LAMBDA) return EPS_ERR_INVALID_ARG;
+  std::vector<Resolved> rs;
+  std::vector<size_t> off;
+  return resolve_batch(n, probs, rs, off, bytes);
+}
+
+eps_status_t eps_forward_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
+                                 float *const *eps, eps_stream_t stream) {
+  std::vector<Resolved> rs;
+  std::vector<size_t> off;
+  size_t total = 0;
+  eps_status_t st = resolve_batch(n, probs, rs, off, &total);
+  if (st != EPS_OK) return st;
+  if (n == 0) return EPS_OK;
+  if (!C || !eps) return EPS_ERR_INVALID_ARG;
+  std::vector<FwdRegion> regions(n);
+  for (int k = 0; k < n; ++k) {
+    if (rs[k].empty) continue;
+    if (probs[k].flags & EPS_FLAG_OFFDIAG) return EPS_ERR_UNSUPPORTED;
+    if (!C[k] || !eps[k] || !aligned(C[k], 4) || !aligned(eps[k], 16)) return EPS_ERR_INVALID_ARG;
+    std::memset(&regions[k], 0, sizeof(FwdRegion));
+    regions[k].g = rs[k].g;
+    regions[k].mode = MODE_FWD;
+    regions[k].write_eps = 1;
+    regions[k].C = C[k];
+    regions[k].eps = eps[k];
+  }
+  int *err = nullptr;
+  if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
+  const BatchTuning t = lookup_tuning(batch_signature(n, probs, -1));
+  return run_fwd_batch(rs, probs, regions, 3, t, err, (cudaStream_t)stream, false);
+}
+
+eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
+                             int32_t n_lambda, int32_t field_type, const void *const *EF,
+                             const void *const *EA, const float *field_scales, float scale,
+                             float *const *dJdC, float *const *eps_out, void *ws, size_t ws_bytes,
+                             eps_stream_t stream) {
+  return vjp_batched_impl(n, probs, C, n_lambda, field_type, EF, EA, field_scales, scale, dJdC,
+                          eps_out, ws, ws_bytes, (cudaStream_t)stream, nullptr);
+}
+
+eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
+                                  int32_t n_lambda, int32_t field_type, const void *const *EF,
+                                  const void *const *EA, const float *field_scales, float scale,
+                                  float *const *dJdC, float *const *eps_out, void *ws,
+                                  size_t ws_bytes, int32_t reps, eps_tuning_t *result,
+                                  eps_stream_t stream) {
+  if (reps < 1 || reps > 1000) return EPS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return EPS_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return EPS_ERR_UNSUPPORTED;   // it synchronises
+  // a dry run with the default shapes checks every argument before timing
+  BatchTuning best = DEFAULT_TUNING;
+  eps_status_t st = vjp_batched_impl(n, probs, C, n_lambda, field_type, EF, EA, field_scales,
+                                     scale, dJdC, eps_out, ws, ws_bytes, s, &best);
+  if (st != EPS_OK) return st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return EPS_ERR_CUDA;
+  }
+  int evals = 0;
+  // mean milliseconds of `reps` calls with shapes t, after one warm-up call
+  auto timeit = [&](const BatchTuning &t, float *ms) -> eps_status_t {
+    eps_status_t r = vjp_batched_impl(n, probs, C, n_lambda, field_type, EF, EA, field_scales,
+                                      scale, dJdC, eps_out, ws, ws_bytes, s, &t);
+    if (r != EPS_OK) return r;
+    if (cudaEventRecord(e0, s) != cudaSuccess) return EPS_ERR_CUDA;
+    for (int i = 0; i < reps && r == EPS_OK; ++i)
+      r = vjp_batched_impl(n, probs, C, n_lambda, field_type, EF, EA, field_scales, scale, dJdC,
+                           eps_out, ws, ws_bytes, s, &t);
+    if (r != EPS_OK) return r;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return EPS_ERR_CUDA;
+    *ms /= reps;
+    ++evals;
+    return EPS_OK;
+  };
+  float best_ms = 0.f, default_ms = 0.f;
+  st = timeit(best, &best_ms);
+  default_ms = best_ms;
+  // coordinate descent over the launch form and shapes, two sweeps
+  for (int sweep = 0; sweep < 2 && st == EPS_OK; ++sweep) {
+    for (int param = 0; param < 5 && st == EPS_OK; ++param) {
+      static const int values[5][4] = {{0, 1, -1, -1}, {1, 3, -1, -1}, {1, 2, 3, 4},
+                                       {1, 2, 3, 4}, {2, 4, 8, 16}};
+      for (int v = 0; v < 4 && st == EPS_OK; ++v) {
+        const int val = values[param][v];
+        if (val < 0) continue;
+        BatchTuning t = best;
+        int *field[5] = {&t.multi, &t.stage_comps, &t.fwd_bps, &t.bwd_bps, &t.contract_bps};
+        if (*field[param] == val) continue;
+        if ((param == 2 || param == 3) && !t.multi) continue;   // grouped form: one block per tile
+        *field[param] = val;
+        float ms = 0.f;
+        st = timeit(t, &ms);
+        if (st == EPS_OK && ms < 0.99f * best_ms) {
+          best = t;
+          best_ms = ms;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != EPS_OK) return st;
+  store_tuning(batch_signature(n, probs, n_lambda), best);
+  if (result) {
+    result->multi = best.multi;
+    result->stencil_blocks_per_sm = best.fwd_bps;
+    result->scatter_blocks_per_sm = best.bwd_bps;
+    result->contract_blocks_per_sm = best.contract_bps;
+    result->stage_components = best.stage_comps;
+    result->evaluations = evals;
+    result->default_ms = default_ms;
+    result->tuned_ms = best_ms;
+  }
+  return EPS_OK;
 }
 
 }  // extern "C"

@@ -208,8 +208,9 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
     gyy = (sUy[h - P + 1] - sUy[h - P - 1]) + 2.f * (sUy[h + 1] - sUy[h - 1]) +
           (sUy[h + P + 1] - sUy[h + P - 1]);
   }
-  const float g2x = gxx * gxx + gyx * gyx;
-  const float g2y = gxy * gxy + gyy * gyy;
+  // explicit fma: the result must not depend on how the compiler contracts
+  const float g2x = fmaf(gxx, gxx, gyx * gyx);
+  const float g2y = fmaf(gxy, gxy, gyy * gyy);
   const bool okx = g2x > NORMAL_TAU2, oky = g2y > NORMAL_TAU2;
   const float ig2x = okx ? __frcp_rn(g2x) : 0.f;
   const float ig2y = oky ? __frcp_rn(g2y) : 0.f;

@@ -32,6 +32,10 @@ const void *pack_entry();
 const void *pack_finish_entry();
 const void *contract_packed_entry();
 
+// Mixed-radius batched stencil / scatter (one persistent launch per phase).
+const void *fwd_multi_entry(int bc);
+const void *bwd_multi_entry(int bc);
+
 // Subpixel-map kernels of the morphology path (kind: MapKind).
 KernelEntry map_entry_a(int rp1, int bc, int kind);
 KernelEntry map_entry_b(int rp1, int bc, int kind);

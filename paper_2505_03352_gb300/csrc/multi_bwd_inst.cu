@@ -1,0 +1,12 @@
+// Instantiation of the mixed-radius batched scatter kernel (both boundary rules).
+#include "epsc_launch.h"
+#include "epsc_multi.cuh"
+
+namespace epsc {
+
+const void *bwd_multi_entry(int bc) {
+  return bc == EPS_BC_CLAMP ? (const void *)&bwd_multi_kernel<EPS_BC_CLAMP>
+                            : (const void *)&bwd_multi_kernel<EPS_BC_PERIODIC>;
+}
+
+}  // namespace epsc

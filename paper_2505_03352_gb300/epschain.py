@@ -124,6 +124,10 @@ _PROTOS = {
     "eps_vjp_real_morph": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP,
                                           ctypes.c_size_t, _VP]),
     "eps_opt_init": (ctypes.c_int, [_VP, _VP, _VP]),
+    "eps_autotune_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(eps_problem_t), _VP,
+                                            ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP,
+                                            ctypes.c_float, _VP, _VP, _VP, ctypes.c_size_t,
+                                            ctypes.c_int32, _VP, _VP]),
     "eps_coarse_workspace_size": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, ctypes.c_int32,
                                                  ctypes.POINTER(ctypes.c_size_t)]),
     "eps_forward_coarse": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP,
@@ -386,6 +390,22 @@ class BatchedVjp:
     def __call__(self, stream=None):
         _check(self._fn(*self._args, _stream(stream)), "eps_vjp_batched")
         return self.dJdC, self.eps
+
+    def autotune(self, reps: int = 5, stream=None) -> dict:
+        """eps_autotune_batched on this batch: times candidate launch shapes,
+        caches the fastest for later calls (and graph captures) of this batch
+        and returns the choice.  Synchronises; call it before capturing."""
+        r = eps_tuning_t()
+        _check(lib().eps_autotune_batched(*self._args, int(reps), ctypes.byref(r), _stream(stream)),
+               "eps_autotune_batched")
+        return {f: getattr(r, f) for f, _ in eps_tuning_t._fields_}
+
+
+class eps_tuning_t(ctypes.Structure):
+    _fields_ = [("multi", ctypes.c_int32), ("stencil_blocks_per_sm", ctypes.c_int32),
+                ("scatter_blocks_per_sm", ctypes.c_int32), ("contract_blocks_per_sm", ctypes.c_int32),
+                ("stage_components", ctypes.c_int32), ("evaluations", ctypes.c_int32),
+                ("default_ms", ctypes.c_float), ("tuned_ms", ctypes.c_float)]
 
 
 def eps_sync_status(stream=None):

@@ -105,3 +105,49 @@ def test_batched_call_in_a_cuda_graph():
     for k in range(len(probs)):
         torch.testing.assert_close(G0[k], ref[k], rtol=0, atol=0)
         torch.testing.assert_close(E0[k], refe[k], rtol=0, atol=0)
+
+
+def test_mixed_radius_classes_need_their_own_launch_set():
+    # radii 5.5 and 6 share the radius class ceil(R) = 6: the batch takes an
+    # extra launch set, and both match their per-region calls
+    import paper_2505_03352_gb300 as ec
+    regs = [dict(mx=64, my=48, nz=16, radius=5.5, beta=8.0, bc=0, seed=3001),
+            dict(mx=40, my=72, nz=16, radius=6.0, beta=16.0, bc=0, seed=3002),
+            dict(mx=36, my=36, nz=16, radius=1.0, beta=8.0, bc=0, seed=3003),
+            dict(mx=50, my=42, nz=16, radius=11.5, beta=32.0, bc=1, seed=3004)]
+    probs, Cs, EF, EA, raw = inputs(regs)
+    G, E = ec.BatchedVjp(probs, Cs, EF, EA)()
+    ec.eps_sync_status()
+    for k, p in enumerate(probs):
+        g1, e1 = ec.eps_vjp(p, Cs[k], EF[k], EA[k], eps_out=True)
+        ec.eps_sync_status()
+        np.testing.assert_array_equal(E[k].cpu().numpy(), e1.cpu().numpy())
+        assert np.max(np.abs(G[k].cpu().numpy() - g1.cpu().numpy())) <= 1e-5 * g1.abs().max().item()
+
+
+def test_autotuned_shapes_give_identical_results():
+    import torch
+
+    import paper_2505_03352_gb300 as ec
+    regs = region_set(n=10, seed=33)
+    probs, Cs, EF, EA, _ = inputs(regs)
+    bv = ec.BatchedVjp(probs, Cs, EF, EA)
+    G0, E0 = bv()
+    G0 = [g.clone() for g in G0]
+    E0 = [e.clone() for e in E0]
+    res = bv.autotune(reps=2)
+    assert res["evaluations"] >= 5 and res["tuned_ms"] <= res["default_ms"] * 1.0001
+    assert res["multi"] in (0, 1) and res["stage_components"] in (1, 3)
+    G1, E1 = bv()          # picks up the cached shapes
+    ec.eps_sync_status()
+    for k in range(len(probs)):
+        assert torch.equal(E0[k], E1[k])
+        assert torch.equal(G0[k], G1[k])
+    # tuning refuses to run while the stream is capturing
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with pytest.raises(ec.EpsError):
+            with torch.cuda.graph(graph, stream=s):
+                bv.autotune(reps=1)
