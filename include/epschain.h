@@ -196,7 +196,10 @@ eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float 
  * per tile (`multi` = 0, the default).  The shapes are: that form, the persistent
  * stencil and scatter blocks per SM, the contraction's blocks per SM, and
  * how many eps_hat components are staged per round of bulk stores (1 or
- * 3; fewer means less shared memory per block).  Results do not depend on
+ * 3; fewer means less shared memory per block), and where the adjoint
+ * seeds (linear in the Eq. 1 column sums W) are finished: in the stencil,
+ * which then waits for the contraction, or by a separate seeds kernel
+ * (`defer_seeds` = 1) so that stencil tiles never wait.  Results do not depend on
  * the shapes (every output element is computed the same way).
  *
  * eps_autotune_batched takes the arguments of eps_vjp_batched plus `reps`
@@ -212,7 +215,7 @@ eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float 
  */
 typedef struct {
   int32_t multi, stencil_blocks_per_sm, scatter_blocks_per_sm, contract_blocks_per_sm;
-  int32_t stage_components, evaluations;
+  int32_t stage_components, defer_seeds, evaluations;
   float default_ms, tuned_ms;
 } eps_tuning_t;
 

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <memory>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -373,6 +374,41 @@ eps_status_t run_contract_packed(const Geometry &g, int n_lambda, int type, cons
   return launch("eps_vjp_contract_packed", contract_packed_entry(), dim3((unsigned)blocks), 0, &pa, s);
 }
 
+// seeds = factor * W over the given regions; launched in plain stream order,
+// so it starts once the contraction and the stencil have both completed
+eps_status_t run_seeds(const SeedsArgs &sa, cudaStream_t s) {
+  int nsm = 0;
+  eps_status_t st = sm_count(&nsm);
+  if (st != EPS_OK) return st;
+  if (sa.ncol == 0) return EPS_OK;
+  const long blocks = std::max<long>(1, std::min<long>((sa.ncol + NTHREADS - 1) / NTHREADS, (long)nsm * 4));
+  return launch("eps_vjp_seeds", seeds_entry(), dim3((unsigned)blocks), 0, (void *)&sa, s, false);
+}
+
+// A single-region VJP defers the seeds to the seeds kernel when the stencil
+// needs more than one wave (more than 3 tiles per SM): stencil blocks then do
+// not hold their SM slots waiting for the contraction while later tiles wait
+// for a slot.  Within one wave, waiting in the stencil saves a launch.
+constexpr int DEFER_SEEDS_TILES_PER_SM = 3;
+
+eps_status_t defer_seeds_for(const Geometry &g, bool *defer) {
+  int nsm = 0;
+  const eps_status_t st = sm_count(&nsm);
+  if (st != EPS_OK) return st;
+  const dim3 grid = fwd_grid(g);
+  *defer = (long)grid.x * grid.y > (long)DEFER_SEEDS_TILES_PER_SM * nsm;
+  return EPS_OK;
+}
+
+eps_status_t run_seeds_one(const Geometry &g, const float *W, float *seeds, cudaStream_t s) {
+  SeedsArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  sa.n = 1;
+  sa.ncol = (long)g.nx * g.ny;
+  sa.r[0] = SeedsRegion{0, sa.ncol, W, seeds};
+  return run_seeds(sa, s);
+}
+
 eps_status_t run_scatter(const Resolved &r, const float *seeds, const float *pd4, const float *ie2,
                          float *dJdC,
                          int *err, cudaStream_t s) {
@@ -543,6 +579,9 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   fa.r.eps = eps_out;
   fa.r.W = Wm;
   fa.r.seeds = seeds;
+  bool defer = false;
+  if ((st = defer_seeds_for(r.g, &defer)) != EPS_OK) return st;
+  fa.r.defer_seeds = defer ? 1 : 0;
   fa.r.pd4 = pd4;
   fa.r.ie2 = ie2;
   const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
@@ -550,7 +589,9 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   st = launch(eps_out ? "eps_fwd_vjp_stencil" : "eps_vjp_stencil", kf.fn, fwd_grid(r.g), smem,
               &fa, s, true);
   if (st != EPS_OK) return st;
-  // 3. transposes down to dJ/dC
+  // 3. (deferred form) seeds = factor * W, once both grids are done
+  if (defer && (st = run_seeds_one(r.g, Wm, seeds, s)) != EPS_OK) return st;
+  // 4. transposes down to dJ/dC
   return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
 }
 
@@ -588,12 +629,16 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
   fa.r.mode = MODE_REAL;
   fa.r.W = Wm;
   fa.r.seeds = seeds;
+  bool defer = false;
+  if ((st = defer_seeds_for(r.g, &defer)) != EPS_OK) return st;
+  fa.r.defer_seeds = defer ? 1 : 0;
   fa.r.pd4 = pd4;
   fa.r.ie2 = ie2;
   const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
   const size_t smem = fwd_smem(kf, r.g, 0, &fa.r.stage_floats);
   st = launch("eps_vjp_real_stencil", kf.fn, fwd_grid(r.g), smem, &fa, s, true);
   if (st != EPS_OK) return st;
+  if (defer && (st = run_seeds_one(r.g, Wm, seeds, s)) != EPS_OK) return st;
   return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
 }
 
@@ -734,11 +779,12 @@ struct BatchTuning {
   int bwd_bps;        // persistent scatter blocks per SM (multi form)
   int contract_bps;   // batched contraction blocks per SM
   int stage_comps;    // eps_hat components staged per round of bulk stores (1 or 3)
+  int defer_seeds;    // 1: stencil writes seed factors, the seeds kernel applies W
 };
 // Default: the grouped form, measured faster on the 64-region batch (radius
 // classes 2 .. 8): one kernel holding all twelve radius bodies runs them side
 // by side on an SM and lost to per-class launches there.
-constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 8, 3};
+constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 8, 3, 0};
 
 std::mutex g_tune_mu;
 std::vector<std::pair<uint64_t, BatchTuning>> g_tune;   // small: one entry per tuned batch
@@ -1022,8 +1068,12 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
   if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
   const BatchTuning t = forced ? *forced : lookup_tuning(batch_signature(n, probs, n_lambda));
 
-  ContractBatchArgs *ca = new ContractBatchArgs;
+  std::unique_ptr<ContractBatchArgs> ca_owner(new ContractBatchArgs);
+  std::unique_ptr<SeedsArgs> sa_owner(new SeedsArgs);
+  ContractBatchArgs *ca = ca_owner.get();
+  SeedsArgs *sa = sa_owner.get();
   std::memset(ca, 0, sizeof(*ca));
+  std::memset(sa, 0, sizeof(*sa));
   std::vector<FwdRegion> fr(n);
   std::vector<BwdRegion> br(n);
   long ncol = 0;
@@ -1035,7 +1085,6 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
     float *out_eps = eps_out ? eps_out[k] : nullptr;
     if (!C[k] || !dJdC[k] || !aligned(C[k], 4) || !aligned(dJdC[k], 4) ||
         (out_eps && !aligned(out_eps, 16)) || (g.nz & 1)) {
-      delete ca;
       return (g.nz & 1) ? EPS_ERR_SHAPE : EPS_ERR_INVALID_ARG;
     }
     const WsLayout L = ws_layout(g);
@@ -1054,7 +1103,6 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
     for (int l = 0; l < n_lambda; ++l) {
       const void *ef = EF[k * n_lambda + l], *ea = EA[k * n_lambda + l];
       if (!ef || !ea || !aligned(ef, 16) || !aligned(ea, 16)) {
-        delete ca;
         return EPS_ERR_INVALID_ARG;
       }
       cr.EF[l] = (const float *)ef;
@@ -1065,17 +1113,18 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
           const float *fsr = field_scales + (size_t)(k * n_lambda + l) * 6;
           sc *= fsr[c] * fsr[3 + c];
           if (!std::isfinite(sc)) {
-            delete ca;
             return EPS_ERR_INVALID_ARG;
           }
         }
         cr.fs[l][c] = sc;
       }
     }
+    sa->r[sa->n++] = SeedsRegion{ncol, (long)g.nx * g.ny, Wm, seeds};
     ncol += (long)g.nx * g.ny;
     fr[k].g = g;
     fr[k].mode = MODE_C64;
     fr[k].write_eps = out_eps ? 1 : 0;
+    fr[k].defer_seeds = t.defer_seeds;
     fr[k].C = C[k];
     fr[k].eps = out_eps;
     fr[k].W = Wm;
@@ -1089,22 +1138,21 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
     br[k].dJdC = dJdC[k];
   }
   ca->ncol = ncol;
+  sa->ncol = ncol;
   if (ncol > 0) {
     int nsm = 0;
-    if ((st = sm_count(&nsm)) != EPS_OK) {
-      delete ca;
-      return st;
-    }
+    if ((st = sm_count(&nsm)) != EPS_OK) return st;
     const long per_block = (NTHREADS / 32) * 4;
     const long blocks = std::max<long>(
         1, std::min<long>((ncol + per_block - 1) / per_block, (long)nsm * t.contract_bps));
     st = launch("eps_batched_contract", contract_batched_entry(), dim3((unsigned)blocks), 0, ca, s);
   }
-  delete ca;
   if (st != EPS_OK) return st;
   bool any_eps = false;
   for (int k = 0; k < n; ++k) any_eps = any_eps || (eps_out && eps_out[k]);
-  if ((st = run_fwd_batch(rs, probs, fr, any_eps ? 3 : 0, t, err, s, true)) != EPS_OK) return st;
+  st = run_fwd_batch(rs, probs, fr, any_eps ? 3 : 0, t, err, s, true);
+  if (st == EPS_OK && t.defer_seeds) st = run_seeds(*sa, s);
+  if (st != EPS_OK) return st;
   return run_bwd_batch(rs, probs, br, t, err, s);
 }
 
@@ -1201,14 +1249,15 @@ eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const f
   default_ms = best_ms;
   // coordinate descent over the launch form and shapes, two sweeps
   for (int sweep = 0; sweep < 2 && st == EPS_OK; ++sweep) {
-    for (int param = 0; param < 5 && st == EPS_OK; ++param) {
-      static const int values[5][4] = {{0, 1, -1, -1}, {1, 3, -1, -1}, {1, 2, 3, 4},
-                                       {1, 2, 3, 4}, {2, 4, 8, 16}};
+    for (int param = 0; param < 6 && st == EPS_OK; ++param) {
+      static const int values[6][4] = {{0, 1, -1, -1}, {1, 3, -1, -1}, {1, 2, 3, 4},
+                                       {1, 2, 3, 4}, {2, 4, 8, 16}, {0, 1, -1, -1}};
       for (int v = 0; v < 4 && st == EPS_OK; ++v) {
         const int val = values[param][v];
         if (val < 0) continue;
         BatchTuning t = best;
-        int *field[5] = {&t.multi, &t.stage_comps, &t.fwd_bps, &t.bwd_bps, &t.contract_bps};
+        int *field[6] = {&t.multi, &t.stage_comps, &t.fwd_bps, &t.bwd_bps, &t.contract_bps,
+                         &t.defer_seeds};
         if (*field[param] == val) continue;
         if ((param == 2 || param == 3) && !t.multi) continue;   // grouped form: one block per tile
         *field[param] = val;
@@ -1231,6 +1280,7 @@ eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const f
     result->scatter_blocks_per_sm = best.bwd_bps;
     result->contract_blocks_per_sm = best.contract_bps;
     result->stage_components = best.stage_comps;
+    result->defer_seeds = best.defer_seeds;
     result->evaluations = evals;
     result->default_ms = default_ms;
     result->tuned_ms = best_ms;

@@ -41,7 +41,8 @@ enum Mode : int { MODE_FWD = 0, MODE_C64 = 1, MODE_REAL = 2 };
 constexpr int ERRFLAG_TIMEOUT = 1;   // a bounded wait gave up
 constexpr int ERRFLAG_BOUNDS = 2;    // a bounds check fired
 
-// seed planes written by the forward/contraction kernel, [NSEED][nx][ny]
+// seed planes, [NSEED][nx][ny]: the stencil writes W-independent factors,
+// the seeds kernel multiplies them by the column's Eq. 1 sums
 enum Seed : int {
   S_DAX = 0, S_DHX, S_GXX, S_GYX,   // x: dJ/dA_x, dJ/dH_x, dJ/dg_x(U_x), dJ/dg_y(U_x)
   S_DAY, S_DHY, S_GXY, S_GYY,       // y: same for U_y
@@ -61,6 +62,8 @@ struct FwdRegion {
   int write_eps;
   int write_offdiag;
   int normals3d;                 // 3-D normals at the slab faces (forward only)
+  int defer_seeds;               // VJP: 1 = write seed factors (the seeds kernel applies W),
+                                 //      0 = wait for the contraction and write the seeds
   int stage_floats;              // shared floats available for eps_hat staging
   const float *C;
   float *eps;
@@ -69,6 +72,19 @@ struct FwdRegion {
   float *seeds;                  // [NSEED][nx][ny]
   float *pd4;                    // [mx][my] P'(u) (eps_core - eps_clad) / 4
   float *ie2;                    // [mx][my] 1 / eps^2
+};
+
+// Seeds kernel: regions laid end to end in one column space.
+struct SeedsRegion {
+  long col_start, ncol;          // first column in the launch's column space, columns
+  const float *W;                // [4][nx][ny] Eq. 1 column sums
+  float *seeds;                  // [NSEED][nx][ny]: factors in, seeds out
+};
+
+struct SeedsArgs {
+  int n;
+  long ncol;
+  SeedsRegion r[EPS_MAX_BATCH];
 };
 
 struct FwdArgs {

@@ -1,5 +1,4 @@
-// Forward chain + Eq. 1 contraction + adjoint seeds, one 8 x 32 tile of Yee
-// columns per block.
+// Forward chain + adjoint seeds, one 8 x 32 tile of Yee columns per block.
 //
 // Stages (all in shared memory except the field reads and the outputs):
 //   1. C tile with a halo of R + 3 subpixels (asynchronous copies), boundary
@@ -11,10 +10,11 @@
 //      the tile plus a one-cell halo; Sobel gradients and normal weights.
 //   4. Eq. 7 per column; eps_hat rows written with warp-contiguous 16-byte
 //      streaming stores.
-//   5. (VJP) the column sums W of Eq. 1 (contraction kernel) are read, and
-//   6. per-column seeds dJ/dA_c, dJ/dH_c, dJ/dg are written to the
-//      workspace; stage 2 already wrote the per-subpixel adjoint factors
-//      P'(u) (eps_core - eps_clad) / 4 and 1/eps^2 of the tile.
+//   5. (VJP) per-column seeds dJ/dA_c, dJ/dH_c, dJ/dg = W * factor, after
+//      waiting for the contraction's column sums W, or (defer_seeds) the
+//      W-independent factors alone, finished by the seeds kernel; stage 2
+//      already wrote the per-subpixel adjoint factors P'(u) (eps_core -
+//      eps_clad) / 4 and 1/eps^2 of the tile.
 #pragma once
 
 #include "epsc_common.cuh"
@@ -362,46 +362,58 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
     return;
   }
 
-  // ---- 5. Eq. 1 contraction sums of this tile's columns ------------------
-  // (computed by the contraction kernel; read them once the grid that wrote
-  // them has completed)
-  griddep_wait();
-  // ---- 6. adjoint seeds -------------------------------------------------
+  // ---- 5. adjoint seeds ----------------------------------------------------
+  // Every adjoint seed of a column is linear in that column's Eq. 1 sum of
+  // its component: seed = W * factor (dJ/dA_z = W_zi itself).  In the
+  // default form the tile waits here for the contraction grid and writes
+  // the seeds; with defer_seeds it writes the W-independent factors and
+  // leaves dJ/dA_z to the seeds kernel, so the stencil never waits (larger
+  // problems: tiles do not hold their SM slot while the fields stream).
+  float fAx = 0.f, fHx = 0.f, fgxx = 0.f, fgyx = 0.f;
+  float fAy = 0.f, fHy = 0.f, fgxy = 0.f, fgyy = 0.f, fHz = 0.f;
   if (valid) {
-    const size_t plane = (size_t)g.nx * g.ny;
-    const float *wc = rg.W + (size_t)ci * g.ny + cj;
-    const float Wx = wc[0 * plane], Wy = wc[1 * plane];
-    const float Wzi = wc[2 * plane], Wzf = wc[3 * plane];
     // eps = 1/(m H + (1-m)/A):  de/dH = -eps^2 m, de/dA = eps^2 (1-m)/A^2, de/dm = -eps^2 (H - 1/A)
-    const float e2x = ex * ex * Wx, e2y = ey * ey * Wy;
-    const float dAx = e2x * (1.f - mx_) * (iAx * iAx), dHx = -e2x * mx_;
-    const float dmx = -e2x * (Hx - iAx);
-    const float dAy = e2y * (1.f - my_) * (iAy * iAy), dHy = -e2y * my_;
-    const float dmy = -e2y * (Hy - iAy);
-    float dgxx = 0.f, dgyx = 0.f, dgxy = 0.f, dgyy = 0.f;
+    const float e2x = ex * ex, e2y = ey * ey;
+    fAx = e2x * (1.f - mx_) * (iAx * iAx);
+    fHx = -e2x * mx_;
+    const float fmx = -e2x * (Hx - iAx);
+    fAy = e2y * (1.f - my_) * (iAy * iAy);
+    fHy = -e2y * my_;
+    const float fmy = -e2y * (Hy - iAy);
     if (okx) {   // m = gx^2/|g|^2: dm/dgx = 2 gx gy^2/|g|^4, dm/dgy = -2 gx^2 gy/|g|^4
-      const float t = 2.f * dmx * (ig2x * ig2x);
-      dgxx = t * gxx * gyx * gyx;
-      dgyx = -t * gxx * gxx * gyx;
+      const float t = 2.f * fmx * (ig2x * ig2x);
+      fgxx = t * gxx * gyx * gyx;
+      fgyx = -t * gxx * gxx * gyx;
     }
     if (oky) {   // m = gy^2/|g|^2: dm/dgx = -2 gx gy^2/|g|^4, dm/dgy = 2 gx^2 gy/|g|^4
-      const float t = 2.f * dmy * (ig2y * ig2y);
-      dgxy = -t * gxy * gyy * gyy;
-      dgyy = t * gxy * gxy * gyy;
+      const float t = 2.f * fmy * (ig2y * ig2y);
+      fgxy = -t * gxy * gyy * gyy;
+      fgyy = t * gxy * gxy * gyy;
     }
-    const float dAz = Wzi;
-    const float dHz = -0.5f * ezf * ezf * Wzf;
+    fHz = -0.5f * ezf * ezf;
+  }
+  float Wx = 1.f, Wy = 1.f, Wzi = 0.f, Wzf = 1.f;
+  if (!rg.defer_seeds) griddep_wait();   // the contraction grid has completed
+  if (valid) {
+    const size_t plane = (size_t)g.nx * g.ny;
+    if (!rg.defer_seeds) {
+      const float *wc = rg.W + (size_t)ci * g.ny + cj;
+      Wx = wc[0 * plane];
+      Wy = wc[1 * plane];
+      Wzi = wc[2 * plane];
+      Wzf = wc[3 * plane];
+    }
     float *sd = rg.seeds + (size_t)ci * g.ny + cj;
-    sd[S_DAX * plane] = dAx;
-    sd[S_DHX * plane] = dHx;
-    sd[S_GXX * plane] = dgxx;
-    sd[S_GYX * plane] = dgyx;
-    sd[S_DAY * plane] = dAy;
-    sd[S_DHY * plane] = dHy;
-    sd[S_GXY * plane] = dgxy;
-    sd[S_GYY * plane] = dgyy;
-    sd[S_DAZ * plane] = dAz;
-    sd[S_DHZ * plane] = dHz;
+    sd[S_DAX * plane] = fAx * Wx;
+    sd[S_DHX * plane] = fHx * Wx;
+    sd[S_GXX * plane] = fgxx * Wx;
+    sd[S_GYX * plane] = fgyx * Wx;
+    sd[S_DAY * plane] = fAy * Wy;
+    sd[S_DHY * plane] = fHy * Wy;
+    sd[S_GXY * plane] = fgxy * Wy;
+    sd[S_GYY * plane] = fgyy * Wy;
+    if (!rg.defer_seeds) sd[S_DAZ * plane] = Wzi;
+    sd[S_DHZ * plane] = fHz * Wzf;
   }
   if (bulk_pending && tid == 0) bulk_wait_all();
 }

@@ -32,6 +32,9 @@ const void *pack_entry();
 const void *pack_finish_entry();
 const void *contract_packed_entry();
 
+// Seeds of Eq. 1 (factor * W), any number of regions.
+const void *seeds_entry();
+
 // Mixed-radius batched stencil / scatter (one persistent launch per phase).
 const void *fwd_multi_entry(int bc);
 const void *bwd_multi_entry(int bc);

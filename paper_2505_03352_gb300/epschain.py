@@ -404,7 +404,8 @@ class BatchedVjp:
 class eps_tuning_t(ctypes.Structure):
     _fields_ = [("multi", ctypes.c_int32), ("stencil_blocks_per_sm", ctypes.c_int32),
                 ("scatter_blocks_per_sm", ctypes.c_int32), ("contract_blocks_per_sm", ctypes.c_int32),
-                ("stage_components", ctypes.c_int32), ("evaluations", ctypes.c_int32),
+                ("stage_components", ctypes.c_int32), ("defer_seeds", ctypes.c_int32),
+                ("evaluations", ctypes.c_int32),
                 ("default_ms", ctypes.c_float), ("tuned_ms", ctypes.c_float)]
 
 
