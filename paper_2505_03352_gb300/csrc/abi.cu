@@ -337,7 +337,8 @@ eps_status_t run_contract_tma(const Geometry &g, int n_lambda, const void *const
     const long nchunks = (ncol + TMA_BY - 1) / TMA_BY;
     const long blocks = std::max<long>(1, std::min<long>(nchunks, (long)nsm * CONTRACT_BLOCKS_PER_SM));
     const size_t smem = (size_t)TMA_NSTAGE * 6 * TMA_BY * bx * 4 + 128;
-    st = launch("eps_vjp_contract", contract_tma_entry(), dim3((unsigned)blocks), smem, ta, s);
+    st = launch("eps_vjp_contract", contract_tma_entry(n_lambda), dim3((unsigned)blocks), smem, ta,
+                s);
   }
   return st;
 }
@@ -381,7 +382,8 @@ eps_status_t run_seeds(const SeedsArgs &sa, cudaStream_t s) {
   eps_status_t st = sm_count(&nsm);
   if (st != EPS_OK) return st;
   if (sa.ncol == 0) return EPS_OK;
-  const long blocks = std::max<long>(1, std::min<long>((sa.ncol + NTHREADS - 1) / NTHREADS, (long)nsm * 4));
+  // one thread per column (a full-occupancy elementwise pass), capped for very large calls
+  const long blocks = std::max<long>(1, std::min<long>((sa.ncol + NTHREADS - 1) / NTHREADS, (long)nsm * 64));
   return launch("eps_vjp_seeds", seeds_entry(), dim3((unsigned)blocks), 0, (void *)&sa, s, false);
 }
 

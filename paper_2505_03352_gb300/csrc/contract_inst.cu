@@ -12,6 +12,11 @@ const void *contract_entry(int lanes) {
 
 const void *contract_batched_entry() { return (const void *)&contract_batched_kernel<0>; }
 
-const void *contract_tma_entry() { return (const void *)&contract_tma_kernel<TMA_NSTAGE>; }
+const void *contract_tma_entry(int n_lambda) {
+  if (n_lambda <= 1) return (const void *)&contract_tma_kernel<TMA_NSTAGE, 2>;
+  if (n_lambda <= 2) return (const void *)&contract_tma_kernel<TMA_NSTAGE, 4>;
+  if (n_lambda <= 4) return (const void *)&contract_tma_kernel<TMA_NSTAGE, 8>;
+  return (const void *)&contract_tma_kernel<TMA_NSTAGE, EPS_MAX_LAMBDA * 2>;
+}
 
 }  // namespace epsc

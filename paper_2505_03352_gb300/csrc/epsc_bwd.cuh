@@ -259,7 +259,7 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
 }
 
 template <int RP1, int BC>
-__global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ BwdArgs a) {
+__global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ BwdArgsR<RP1> a) {
   bwd_tile<RP1, BC>(a, a.r, blockIdx.y * TA, blockIdx.x * TB);
 }
 

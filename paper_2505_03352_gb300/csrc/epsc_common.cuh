@@ -87,11 +87,20 @@ struct SeedsArgs {
   SeedsRegion r[EPS_MAX_BATCH];
 };
 
-struct FwdArgs {
+// Kernel arguments end with the conic weights, a dense (2 RP1 - 1)^2 box,
+// row-major.  Each kernel takes the struct with exactly its box (NW = (2 RP1
+// - 1)^2); the host fills the full-size struct (NW = MAX_BOX^2) and passes
+// it, and the launch copies only the kernel's parameter bytes, a common
+// prefix.  Smaller parameter blocks launch faster.
+template <int NW>
+struct FwdArgsN {
   FwdRegion r;
   int *err;
-  float w[MAX_BOX * MAX_BOX];    // conic weights, dense (2 RP1 - 1)^2 box, row-major
+  float w[NW];
 };
+using FwdArgs = FwdArgsN<MAX_BOX * MAX_BOX>;
+template <int RP1>
+using FwdArgsR = FwdArgsN<(2 * RP1 - 1) * (2 * RP1 - 1)>;
 
 // Batched stencil launch: regions sharing one conic filter; block b works on
 // tile b - tile_start[k] of region k, tile_start[k] <= b < tile_start[k+1].
@@ -113,11 +122,15 @@ struct BwdRegion {
   float *dJdC;
 };
 
-struct BwdArgs {
+template <int NW>
+struct BwdArgsN {
   BwdRegion r;
   int *err;
-  float w[MAX_BOX * MAX_BOX];
+  float w[NW];
 };
+using BwdArgs = BwdArgsN<MAX_BOX * MAX_BOX>;
+template <int RP1>
+using BwdArgsR = BwdArgsN<(2 * RP1 - 1) * (2 * RP1 - 1)>;
 
 struct BwdBatchArgs {
   int n;

@@ -26,15 +26,21 @@ constexpr int TMA_BY = 32;        // columns per box
 constexpr int TMA_NSTAGE = 2; // ring depth
 constexpr int TMA_BX_MAX = 64;    // floats per box row (support window)
 
-struct __align__(64) ContractTmaArgs {
-  CUtensorMap maps[EPS_MAX_LAMBDA * 2];   // [wavelength][field F/A]
-  float fs[EPS_MAX_LAMBDA][3];
+// The tensor maps come last: the kernel is instantiated for 2, 4, 8 or
+// 2 EPS_MAX_LAMBDA maps and takes only its own count; the host fills the
+// full-size struct and the launch copies the kernel's parameter bytes, a
+// common prefix (smaller parameter blocks launch faster).
+template <int NMAPS>
+struct __align__(64) ContractTmaArgsN {
   float *W;                                // [4][nx][ny]
   int *err;
   int nx, ny, k0, nk, nlambda;
   int x0;                                  // first float of the window in a column
   int bx;                                  // window width in floats (multiple of 8)
+  float fs[EPS_MAX_LAMBDA][3];
+  CUtensorMap maps[NMAPS];                 // [wavelength][field F/A]
 };
+using ContractTmaArgs = ContractTmaArgsN<EPS_MAX_LAMBDA * 2>;
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -84,8 +90,8 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 
 // dynamic shared memory: NSTAGE stages of 6 * TMA_BY * bx floats, plus
 // 128 bytes of slack to align the ring to 128 bytes
-template <int NSTAGE>
-__global__ void __launch_bounds__(NTHREADS) contract_tma_kernel(const __grid_constant__ ContractTmaArgs a) {
+template <int NSTAGE, int NMAPS>
+__global__ void __launch_bounds__(NTHREADS) contract_tma_kernel(const __grid_constant__ ContractTmaArgsN<NMAPS> a) {
   extern __shared__ float smem_raw[];
   __shared__ uint64_t full[NSTAGE];
   __shared__ int s_abort;

@@ -419,7 +419,7 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
 }
 
 template <int RP1, int BC>
-__global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant__ FwdArgs a) {
+__global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant__ FwdArgsR<RP1> a) {
   fwd_tile<RP1, BC>(a, a.r, blockIdx.y * TI, blockIdx.x * TJ);
 }
 

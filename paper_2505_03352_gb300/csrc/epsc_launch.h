@@ -23,8 +23,9 @@ KernelEntry bwd_entry_b(int rp1, int bc, bool batched);
 const void *contract_entry(int lanes);
 // Contraction over many regions in one launch.
 const void *contract_batched_entry();
-// Contraction kernel fed by bulk tensor copies (complex64 fields).
-const void *contract_tma_entry();
+// Contraction kernel fed by bulk tensor copies (complex64 fields), with room
+// for at least n_lambda wavelengths' tensor maps.
+const void *contract_tma_entry(int n_lambda);
 
 // Reduced-precision field path.
 const void *pack_amax_entry();
