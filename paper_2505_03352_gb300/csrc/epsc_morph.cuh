@@ -29,7 +29,10 @@ constexpr int NA_M = 4;               // outputs per strip
 
 enum MapKind { MAP_FRONT = 0, MAP_LSE = 1, MAP_LSE_T = 2, MAP_FRONT_T = 3 };
 
-struct MapArgs {
+// The weights come last: each kernel takes the struct with its own (2 RP1 -
+// 1)^2 box, the host fills the full-size one (a common prefix).
+template <int NW>
+struct MapArgsN {
   int mx, my;
   float beta, eta;      // FRONT: first projection (Eq. 3)
   float alpha;          // LSE, LSE_T
@@ -39,8 +42,9 @@ struct MapArgs {
   const float *aux2;    // LSE_T: rho_k
   float *out;           // FRONT: rho_0; LSE: rho_{k+1}; LSE_T: g_k; FRONT_T: dJ/dC
   float *out2;          // FRONT: P'(u)
-  float w[MAX_BOX * MAX_BOX];
+  float w[NW];
 };
+using MapArgs = MapArgsN<MAX_BOX * MAX_BOX>;
 
 template <int RP1>
 struct MapSmem {
@@ -59,7 +63,8 @@ struct MapSmem {
 __device__ __forceinline__ float lse_s(float rho, int erode) { return erode ? 1.f - rho : rho; }
 
 template <int RP1, int BC, int KIND>
-__global__ void __launch_bounds__(NTHREADS) map_kernel(const __grid_constant__ MapArgs a) {
+__global__ void __launch_bounds__(NTHREADS) map_kernel(
+    const __grid_constant__ MapArgsN<(2 * RP1 - 1) * (2 * RP1 - 1)> a) {
   using S = MapSmem<RP1>;
   constexpr int R = S::R;
   constexpr bool TRANS = KIND == MAP_LSE_T || KIND == MAP_FRONT_T;
