@@ -219,6 +219,16 @@ typedef struct {
   float default_ms, tuned_ms;
 } eps_tuning_t;
 
+/*
+ * eps_batched_set_tuning stores launch shapes for a batch directly (the same
+ * cache eps_autotune_batched fills; evaluations, default_ms and tuned_ms are
+ * ignored).  n_lambda is the wavelength count of the eps_vjp_batched calls
+ * it applies to, or -1 for eps_forward_batched.  Fields: multi 0 or 1,
+ * blocks per SM 1 .. 16 (stencil, scatter) and 1 .. 64 (contraction),
+ * stage_components 1 or 3, defer_seeds 0 or 1; else EPS_ERR_INVALID_ARG.
+ */
+eps_status_t eps_batched_set_tuning(int32_t n, const eps_problem_t *probs, int32_t n_lambda,
+                                   const eps_tuning_t *tuning);
 eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
                                   int32_t n_lambda, int32_t field_type, const void *const *EF,
                                   const void *const *EA, const float *field_scales, float scale,

@@ -1207,6 +1207,22 @@ eps_status_t eps_vjp_batched(int32_t n, const eps_problem_t *probs, const float 
                           eps_out, ws, ws_bytes, (cudaStream_t)stream, nullptr);
 }
 
+eps_status_t eps_batched_set_tuning(int32_t n, const eps_problem_t *probs, int32_t n_lambda,
+                                   const eps_tuning_t *tuning) {
+  if (!tuning || n < 0 || n > EPS_MAX_BATCH || (n > 0 && !probs)) return EPS_ERR_INVALID_ARG;
+  if (n_lambda < -1 || n_lambda > EPS_MAX_BATCH_LAMBDA) return EPS_ERR_INVALID_ARG;
+  const eps_tuning_t &u = *tuning;
+  if ((u.multi != 0 && u.multi != 1) || u.stencil_blocks_per_sm < 1 || u.stencil_blocks_per_sm > 16 ||
+      u.scatter_blocks_per_sm < 1 || u.scatter_blocks_per_sm > 16 || u.contract_blocks_per_sm < 1 ||
+      u.contract_blocks_per_sm > 64 || (u.stage_components != 1 && u.stage_components != 3) ||
+      (u.defer_seeds != 0 && u.defer_seeds != 1))
+    return EPS_ERR_INVALID_ARG;
+  const BatchTuning t{u.multi, u.stencil_blocks_per_sm, u.scatter_blocks_per_sm,
+                      u.contract_blocks_per_sm, u.stage_components, u.defer_seeds};
+  store_tuning(batch_signature(n, probs, n_lambda), t);
+  return EPS_OK;
+}
+
 eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const float *const *C,
                                   int32_t n_lambda, int32_t field_type, const void *const *EF,
                                   const void *const *EA, const float *field_scales, float scale,

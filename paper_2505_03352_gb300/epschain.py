@@ -124,6 +124,8 @@ _PROTOS = {
     "eps_vjp_real_morph": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP, _VP,
                                           ctypes.c_size_t, _VP]),
     "eps_opt_init": (ctypes.c_int, [_VP, _VP, _VP]),
+    "eps_batched_set_tuning": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(eps_problem_t),
+                                              ctypes.c_int32, _VP]),
     "eps_autotune_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(eps_problem_t), _VP,
                                             ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP,
                                             ctypes.c_float, _VP, _VP, _VP, ctypes.c_size_t,
@@ -390,6 +392,20 @@ class BatchedVjp:
     def __call__(self, stream=None):
         _check(self._fn(*self._args, _stream(stream)), "eps_vjp_batched")
         return self.dJdC, self.eps
+
+    def set_tuning(self, **shapes):
+        """Store launch shapes for this batch (eps_batched_set_tuning); keys are
+        the eps_tuning_t fields multi, stencil_blocks_per_sm,
+        scatter_blocks_per_sm, contract_blocks_per_sm, stage_components and
+        defer_seeds (defaults: the library's default shapes)."""
+        r = eps_tuning_t()
+        base = dict(multi=0, stencil_blocks_per_sm=3, scatter_blocks_per_sm=3,
+                    contract_blocks_per_sm=8, stage_components=3, defer_seeds=0)
+        base.update(shapes)
+        for k, v in base.items():
+            setattr(r, k, int(v))
+        n, probs, nl = self._args[0], self._args[1], self._args[3]
+        _check(lib().eps_batched_set_tuning(n, probs, nl, ctypes.byref(r)), "eps_batched_set_tuning")
 
     def autotune(self, reps: int = 5, stream=None) -> dict:
         """eps_autotune_batched on this batch: times candidate launch shapes,

@@ -151,3 +151,41 @@ def test_autotuned_shapes_give_identical_results():
         with pytest.raises(ec.EpsError):
             with torch.cuda.graph(graph, stream=s):
                 bv.autotune(reps=1)
+
+
+@pytest.mark.parametrize("shapes", [
+    dict(multi=1),                                        # persistent mixed-radius launches
+    dict(multi=1, stencil_blocks_per_sm=1, scatter_blocks_per_sm=2, stage_components=1),
+    dict(multi=0, defer_seeds=1),                         # seeds finished by the seeds kernel
+    dict(multi=1, defer_seeds=1, contract_blocks_per_sm=2),
+])
+def test_every_launch_form_equals_per_region_calls(shapes):
+    import paper_2505_03352_gb300 as ec
+    regs = region_set(n=12, seed=41)
+    regs[3]["radius"], regs[4]["radius"] = 5.5, 6.0      # one radius class twice
+    probs, Cs, EF, EA, raw = inputs(regs)
+    bv = ec.BatchedVjp(probs, Cs, EF, EA)
+    bv.set_tuning(**shapes)
+    G, E = bv()
+    ec.eps_sync_status()
+    for k, p in enumerate(probs):
+        g1, e1 = ec.eps_vjp(p, Cs[k], EF[k], EA[k], eps_out=True)
+        ec.eps_sync_status()
+        np.testing.assert_array_equal(E[k].cpu().numpy(), e1.cpu().numpy())
+        assert np.max(np.abs(G[k].cpu().numpy() - g1.cpu().numpy())) <= 1e-5 * g1.abs().max().item()
+    # and one region against the oracle directly
+    C, ef, ea = raw[5]
+    p = probs[5]
+    o = orc.Problem(mx=p.mx, my=p.my, nz=p.nz, radius=p.radius, beta=p.beta, bc=p.bc)
+    ref = orc.vjp_fields(o, C, [ef], [ea])
+    assert np.max(np.abs(G[5].cpu().numpy() - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+def test_bad_tuning_is_rejected():
+    import paper_2505_03352_gb300 as ec
+    probs, Cs, EF, EA, _ = inputs(region_set(n=2, seed=43))
+    bv = ec.BatchedVjp(probs, Cs, EF, EA)
+    for bad in (dict(multi=2), dict(stage_components=2), dict(stencil_blocks_per_sm=0),
+                dict(defer_seeds=5), dict(contract_blocks_per_sm=65)):
+        with pytest.raises(ec.EpsError):
+            bv.set_tuning(**bad)

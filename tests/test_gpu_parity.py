@@ -260,3 +260,21 @@ def test_l2_fetch_granularity_does_not_change_results():
     g, e = run_vjp(p, C, EF, EA)
     np.testing.assert_array_equal(g32, g)
     np.testing.assert_array_equal(e32, e)
+
+
+def test_multi_wave_problem_defers_the_seeds_and_matches_the_oracle():
+    # 800 x 720 controls: 50 x 12 stencil tiles, more than 3 per SM, so the
+    # stencil writes seed factors and the seeds kernel applies W
+    rng = np.random.default_rng(12)
+    p, o = problems(800, 720, 16, 4.0, 16.0)
+    C = synth.soi_layout(800, 720, 1212)
+    shape = (3, p.nx, p.ny, p.nz)
+    EF = [synth.complex_field(shape, 1213)]
+    EA = [synth.complex_field(shape, 1214)]
+    check_case(p, o, C, EF, EA)
+    G = rng.standard_normal(shape).astype(np.float32)
+    ec = _ec()
+    got = ec.eps_vjp_real(p, to_dev(C), to_dev(G)).cpu().numpy()
+    ec.eps_sync_status()
+    ref = orc.vjp_real(o, C, G.astype(np.float64))
+    assert grad_err(got, ref) <= GRAD_TOL
