@@ -103,10 +103,11 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
   __syncthreads();
 
   // ---- 2. filtered density, projection, mixing -------------------------
-  // rho = (1 + tanh(x)) / 2 = 1 / (1 + exp(-2x)), x = beta (u - eta); the
-  // adjoint factor P'(u) (eps_core - eps_clad) / 4 = beta/2 deps rho (1 - rho)
-  // with 1 - rho = exp(-2x) rho, and 1/eps^2 of the core subpixels go to the
-  // workspace for the scatter kernel.
+  // rho = (1 + tanh(x)) / 2, x = beta (u - eta), from t = exp(-2|x|) <= 1
+  // (no overflow at any beta): rho = 1/(1+t) for x >= 0 and t/(1+t) below,
+  // rho (1 - rho) = t/(1+t)^2.  The adjoint factor P'(u) (eps_core -
+  // eps_clad) / 4 = beta/2 deps rho (1 - rho) and 1/eps^2 of the core
+  // subpixels go to the workspace for the scatter kernel.
   constexpr int NSTRIP = UA / NA_F;
   const bool vjp = rg.mode != MODE_FWD;
   for (int item = tid; item < NSTRIP * UB; item += NTHREADS) {
@@ -119,8 +120,9 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
     for (int k = 0; k < NA_F; ++k) {
       const int o = (r0 + k) * UB + col;
       const float x = g.beta * (hi[k] - g.eta);
-      const float ex2 = __expf(-2.f * x);
-      const float rho = __fdividef(1.f, 1.f + ex2);
+      const float t = __expf(-2.f * fabsf(x));
+      const float inv = __fdividef(1.f, 1.f + t);
+      const float rho = x >= 0.f ? inv : t * inv;
       const float e = fmaf(rho, g.deps, g.eps_clad);
       const float ie = __frcp_rn(e);
       su[o] = hi[k];
@@ -130,7 +132,7 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
         const int ra = r0 + k - 3, rb = col - 3;   // core subpixel of the tile?
         if (ra >= 0 && ra < 2 * nvi && rb >= 0 && rb < 2 * nvj) {
           const size_t go = (size_t)(2 * i0 + ra) * g.my + 2 * j0 + rb;
-          rg.pd4[go] = 0.5f * g.beta * g.deps * (ex2 * rho * rho);
+          rg.pd4[go] = 0.5f * g.beta * g.deps * (t * inv * inv);
           rg.ie2[go] = ie * ie;
         }
       }

@@ -278,3 +278,23 @@ def test_multi_wave_problem_defers_the_seeds_and_matches_the_oracle():
     ec.eps_sync_status()
     ref = orc.vjp_real(o, C, G.astype(np.float64))
     assert grad_err(got, ref) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_large_beta_stays_finite_and_close(bc):
+    # beta = 200 (beyond the stated beta <= 32 range, reached by the beta
+    # schedule of the optimiser): exp(-2 beta (u - eta)) would overflow FP32,
+    # the kernels use exp(-2|x|) instead.  The projection slope (up to
+    # beta / 2 = 100) amplifies the FP32 rounding of u, hence the looser bound.
+    rng = np.random.default_rng(13)
+    p, o = problems(70, 66, 16, 3.0, 200.0, bc=bc)
+    C = rng.random((70, 66), dtype=np.float32)
+    shape = (3, p.nx, p.ny, p.nz)
+    EF = [synth.complex_field(shape, 1301)]
+    EA = [synth.complex_field(shape, 1302)]
+    g, e = run_vjp(p, C, EF, EA)
+    assert np.all(np.isfinite(g)) and np.all(np.isfinite(e))
+    ref = orc.forward(o, C)["eps_hat"]
+    ref_g = orc.vjp_fields(o, C, EF, EA)
+    assert eps_err(e, ref) <= 1e-3
+    assert grad_err(g, ref_g) <= 1e-2
