@@ -223,6 +223,7 @@ eps_status_t error_flag_ptr(int **out) {
 }
 
 dim3 fwd_grid(const Geometry &g) { return dim3((g.ny + TJ - 1) / TJ, (g.nx + TI - 1) / TI); }
+long fwd_ntiles(const Geometry &g) { return (long)fwd_grid(g).x * fwd_grid(g).y; }
 dim3 bwd_grid(const Geometry &g) { return dim3((g.my + TB - 1) / TB, (g.mx + TA - 1) / TA); }
 
 // Dynamic shared memory of a forward launch: the stencil buffers, grown to
@@ -387,18 +388,27 @@ eps_status_t run_seeds(const SeedsArgs &sa, cudaStream_t s) {
   return launch("eps_vjp_seeds", seeds_entry(), dim3((unsigned)blocks), 0, (void *)&sa, s, false);
 }
 
-// A single-region VJP defers the seeds to the seeds kernel when the stencil
-// needs more than one wave (more than 3 tiles per SM): stencil blocks then do
-// not hold their SM slots waiting for the contraction while later tiles wait
-// for a slot.  Within one wave, waiting in the stencil saves a launch.
-constexpr int DEFER_SEEDS_TILES_PER_SM = 3;
+// Launch form of a single-region VJP stencil (one block per tile): where
+// the seeds are finished (0: each tile waits for the contraction; 1: the
+// seeds kernel) and the eps_hat components staged per round.  Within one
+// wave (at most 3 tiles per SM) waiting in the tile saves a launch; larger
+// problems defer, so tiles never hold an SM slot while the fields stream.
+// (Measured alternatives that lost: a persistent stencil of 2 or 3 blocks
+// per SM finishing its seeds after its last tile, and 1-component staging.)
+struct StencilForm {
+  int defer, stage_comps;
+};
+constexpr int ONE_WAVE_TILES_PER_SM = 3;
+constexpr StencilForm FORM_ONE_WAVE{0, 3};
+constexpr StencilForm FORM_MULTI_WAVE{1, 3};
 
-eps_status_t defer_seeds_for(const Geometry &g, bool *defer) {
+eps_status_t stencil_form(const Geometry &g, StencilForm *f, long *blocks) {
   int nsm = 0;
   const eps_status_t st = sm_count(&nsm);
   if (st != EPS_OK) return st;
-  const dim3 grid = fwd_grid(g);
-  *defer = (long)grid.x * grid.y > (long)DEFER_SEEDS_TILES_PER_SM * nsm;
+  const long tiles = fwd_ntiles(g);
+  *f = tiles <= (long)ONE_WAVE_TILES_PER_SM * nsm ? FORM_ONE_WAVE : FORM_MULTI_WAVE;
+  *blocks = tiles;
   return EPS_OK;
 }
 
@@ -477,7 +487,7 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps, 
   fa.r.offdiag = od ? offdiag : nullptr;
   const KernelEntry k = fwd_entry(r.rp1, r.g.bc);
   const size_t smem = fwd_smem(k, r.g, od ? 5 : 3, &fa.r.stage_floats);
-  return launch("eps_forward", k.fn, fwd_grid(r.g), smem, &fa, (cudaStream_t)stream);
+  return launch("eps_forward", k.fn, dim3((unsigned)fwd_ntiles(r.g)), smem, &fa, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -581,18 +591,20 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   fa.r.eps = eps_out;
   fa.r.W = Wm;
   fa.r.seeds = seeds;
-  bool defer = false;
-  if ((st = defer_seeds_for(r.g, &defer)) != EPS_OK) return st;
-  fa.r.defer_seeds = defer ? 1 : 0;
+  StencilForm form;
+  long blocks = 0;
+  if ((st = stencil_form(r.g, &form, &blocks)) != EPS_OK) return st;
+  fa.r.defer_seeds = form.defer;
   fa.r.pd4 = pd4;
   fa.r.ie2 = ie2;
   const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
-  const size_t smem = fwd_smem(kf, r.g, eps_out ? 3 : 0, &fa.r.stage_floats);
-  st = launch(eps_out ? "eps_fwd_vjp_stencil" : "eps_vjp_stencil", kf.fn, fwd_grid(r.g), smem,
-              &fa, s, true);
+  const size_t smem =
+      fwd_smem(kf, r.g, eps_out ? std::min(3, form.stage_comps) : 0, &fa.r.stage_floats);
+  st = launch(eps_out ? "eps_fwd_vjp_stencil" : "eps_vjp_stencil", kf.fn, dim3((unsigned)blocks),
+              smem, &fa, s, true);
   if (st != EPS_OK) return st;
-  // 3. (deferred form) seeds = factor * W, once both grids are done
-  if (defer && (st = run_seeds_one(r.g, Wm, seeds, s)) != EPS_OK) return st;
+  // 3. (seeds-kernel form) seeds = factor * W, once both grids are done
+  if (form.defer == 1 && (st = run_seeds_one(r.g, Wm, seeds, s)) != EPS_OK) return st;
   // 4. transposes down to dJ/dC
   return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
 }
@@ -631,16 +643,17 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
   fa.r.mode = MODE_REAL;
   fa.r.W = Wm;
   fa.r.seeds = seeds;
-  bool defer = false;
-  if ((st = defer_seeds_for(r.g, &defer)) != EPS_OK) return st;
-  fa.r.defer_seeds = defer ? 1 : 0;
+  StencilForm form;
+  long blocks = 0;
+  if ((st = stencil_form(r.g, &form, &blocks)) != EPS_OK) return st;
+  fa.r.defer_seeds = form.defer;
   fa.r.pd4 = pd4;
   fa.r.ie2 = ie2;
   const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
   const size_t smem = fwd_smem(kf, r.g, 0, &fa.r.stage_floats);
-  st = launch("eps_vjp_real_stencil", kf.fn, fwd_grid(r.g), smem, &fa, s, true);
+  st = launch("eps_vjp_real_stencil", kf.fn, dim3((unsigned)blocks), smem, &fa, s, true);
   if (st != EPS_OK) return st;
-  if (defer && (st = run_seeds_one(r.g, Wm, seeds, s)) != EPS_OK) return st;
+  if (form.defer == 1 && (st = run_seeds_one(r.g, Wm, seeds, s)) != EPS_OK) return st;
   return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
 }
 

@@ -62,8 +62,8 @@ struct FwdRegion {
   int write_eps;
   int write_offdiag;
   int normals3d;                 // 3-D normals at the slab faces (forward only)
-  int defer_seeds;               // VJP: 1 = write seed factors (the seeds kernel applies W),
-                                 //      0 = wait for the contraction and write the seeds
+  int defer_seeds;               // VJP: 0 = wait for the contraction and write the seeds,
+                                 //      1 = write seed factors (the seeds kernel applies W)
   int stage_floats;              // shared floats available for eps_hat staging
   const float *C;
   float *eps;

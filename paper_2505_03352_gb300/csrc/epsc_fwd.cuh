@@ -420,9 +420,19 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
   if (bulk_pending && tid == 0) bulk_wait_all();
 }
 
+// Single-region stencil over a 1-D grid: block b takes tiles b,
+// b + gridDim.x, ... of the row-major tile grid (one tile per block when the
+// grid covers them all).
 template <int RP1, int BC>
 __global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant__ FwdArgsR<RP1> a) {
-  fwd_tile<RP1, BC>(a, a.r, blockIdx.y * TI, blockIdx.x * TJ);
+  const Geometry &g = a.r.g;
+  const int tiles_j = (g.ny + TJ - 1) / TJ;
+  const int ntiles = tiles_j * ((g.nx + TI - 1) / TI);
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int ti = t / tiles_j;
+    fwd_tile<RP1, BC>(a, a.r, ti * TI, (t - ti * tiles_j) * TJ);
+    __syncthreads();   // the next tile reuses shared memory (bulk stores have drained)
+  }
 }
 
 template <int RP1, int BC>
