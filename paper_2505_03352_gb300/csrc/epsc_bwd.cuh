@@ -225,8 +225,8 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
     for (int item = tid; item < NSTRIP * GB; item += NTHREADS) {
       const int st = (int)dgb.div((unsigned)item), col = item - st * GB;
       const int r0 = st * NA_B;
-      float hi[NA_B], lo[NA_B];
-      strip_stencil<RP1, NA_B, false>(sU + r0 * DBP + col, DBP, a, hi, lo);
+      float hi[NA_B];
+      strip_stencil<RP1, NA_B>(sU + r0 * DBP + col, DBP, a, hi);
 #pragma unroll
       for (int k = 0; k < NA_B; ++k) {
         if (r0 + k < GA) sdc[(r0 + k) * S::GB_MAX + col] = hi[k];

@@ -204,33 +204,22 @@ __device__ __forceinline__ void griddep_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
-// Knuth's TwoSum: hi + lo += x with the rounding error of the add kept in lo.
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
-  const float s = hi + x;
-  const float bb = s - hi;
-  const float err = (hi - (s - bb)) + (x - bb);
-  hi = s;
-  lo += err;
-}
-
 // Register-blocked conic stencil over a strip of NA outputs stacked along the
 // row direction.  `src` points at the input element that lies R rows above and
 // R columns left of output 0; output k is
 //     sum_{p,q} w[(p+R)(2R+1) + q+R] * src[(k + p + R) * pitch + q + R].
 // Every input row is read once from shared memory and reused by all NA
-// outputs.  With COMP the per-row partial sums are accumulated with TwoSum
-// (hi + lo), which keeps u accurate to about one ulp where the projection
-// amplifies its error by up to beta/2.
-template <int RP1, int NA, bool COMP, class Args>
+// outputs.  Each output adds the per-row partial sums of its taps: fewer
+// rounding steps in sequence than one long fma chain, which matters where a
+// projection amplifies u's error by up to beta/2 (twice on the morphology
+// path).
+template <int RP1, int NA, class Args>
 __device__ __forceinline__ void strip_stencil(const float *__restrict__ src, int pitch,
-                                              const Args &a, float (&hi)[NA], float (&lo)[NA]) {
+                                              const Args &a, float (&out)[NA]) {
   constexpr int R = RP1 - 1;
   constexpr int BW = 2 * R + 1;
 #pragma unroll
-  for (int k = 0; k < NA; ++k) {
-    hi[k] = 0.f;
-    lo[k] = 0.f;
-  }
+  for (int k = 0; k < NA; ++k) out[k] = 0.f;
 #pragma unroll
   for (int rr = 0; rr < NA + 2 * R; ++rr) {
     float v[BW];
@@ -245,10 +234,7 @@ __device__ __forceinline__ void strip_stencil(const float *__restrict__ src, int
         for (int q = -R; q <= R; ++q) {
           if (p * p + q * q < RP1 * RP1) part = fmaf(a.w[(p + R) * BW + q + R], v[q + R], part);
         }
-        if (COMP)
-          two_sum_acc(hi[k], lo[k], part);
-        else
-          hi[k] += part;
+        out[k] += part;
       }
     }
   }

@@ -114,8 +114,8 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
     const int s = item / UB;
     const int col = item - s * UB;
     const int r0 = s * NA_F;
-    float hi[NA_F], lo[NA_F];
-    strip_stencil<RP1, NA_F, false>(sC + r0 * CB + col, CB, a, hi, lo);
+    float hi[NA_F];
+    strip_stencil<RP1, NA_F>(sC + r0 * CB + col, CB, a, hi);
 #pragma unroll
     for (int k = 0; k < NA_F; ++k) {
       const int o = (r0 + k) * UB + col;

@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(NTHREADS) map_kernel(
   for (int item = tid; item < NSTRIP * GB; item += NTHREADS) {
     const int st = item / GB, col = item - st * GB;
     const int r0 = st * NA_M;
-    float hi[NA_M], lo[NA_M];
-    strip_stencil<RP1, NA_M, false>(sIn + r0 * S::SP + col, S::SP, a, hi, lo);
+    float hi[NA_M];
+    strip_stencil<RP1, NA_M>(sIn + r0 * S::SP + col, S::SP, a, hi);
 #pragma unroll
     for (int k = 0; k < NA_M; ++k) {
       const int r = r0 + k;

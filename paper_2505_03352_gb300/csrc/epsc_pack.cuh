@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(NTHREADS) contract_packed_kernel(const __grid_
       for (int c = 0; c < 3; ++c) {
         const size_t base = ((size_t)c * ncol + col) * nq;
         float s_in = 0.f, s_face = 0.f;
-        for (int q = 0; q < nq; ++q) {
+#pragma unroll 4
+        for (int q = 0; q < nq; ++q) {   // unrolled: more loads in flight per thread
           const uint4 f = __ldg(pf + base + q);
           const uint4 e = __ldg(pa + base + q);
           const unsigned fb[4] = {f.x, f.y, f.z, f.w};
