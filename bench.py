@@ -69,6 +69,36 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def link_floor(torch, dev, stream, h2d_bytes: int, d2h_bytes: int, reps: int = 10) -> dict:
+    """The host link's copy rates, measured on plain pinned buffers of the
+    step's own sizes, and the per-step time floor they set for the
+    end-to-end loop: the two directions run concurrently across consecutive
+    steps, so the floor is the slower direction's time."""
+    def rate(nbytes: int, to_device: bool) -> float:
+        host = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        devb = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        dst, src = (devb, host) if to_device else (host, devb)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            e0.record(stream)
+            for _ in range(reps):
+                dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        del host, devb
+        return nbytes / (ms * 1e-3) / 1e9
+    g_in = rate(h2d_bytes, True)
+    g_out = rate(d2h_bytes, False)
+    floor = max(h2d_bytes / (g_in * 1e9), d2h_bytes / (g_out * 1e9)) * 1e3
+    return {"h2d_gbs": round(g_in, 1), "d2h_gbs": round(g_out, 1),
+            "floor_ms_per_step": round(floor, 4),
+            "note": "pinned-buffer copy rates of the step's byte counts; frac = floor / e2e ms per step"}
+
+
 def weak_scaling_value(units_per_rank: float, world: int, steps: int, ms_total_max: float) -> float:
     """Whole-job throughput: every rank processes its own units each step,
     and the job takes as long as its slowest rank."""
@@ -393,11 +423,15 @@ def run_ours(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        ms_e2e = ms / args.e2e_steps
+        link = link_floor(torch, dev, stream, h2d, d2h)
+        link["frac"] = round(link["floor_ms_per_step"] / ms_e2e, 4)
         e2e = {"value": weak_scaling_value(w.voxels, world, args.e2e_steps, ms), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": round(ms / args.e2e_steps, 4),
+               "ms_per_step": round(ms_e2e, 4),
                "path": ("pinned host -> device copies, eps_vjp, device -> host copies; "
-                        "two streams with double buffers, consecutive steps overlap")}
+                        "two streams with double buffers, consecutive steps overlap"),
+               "link": link}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
