@@ -445,6 +445,7 @@ def run_ours(args, rank, world, local):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
+            "controls_per_s": round(world * w.mx * w.my / (ms_step * 1e-3), 1),
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "controls": [w.mx, w.my],
                        "yee": [w.nx, w.ny, w.nz], "radius_px": w.radius, "beta": w.beta,
@@ -540,6 +541,7 @@ def run_variants(torch, ec, synth, dev, flush_l2,
         alg = algorithmic_bytes(w, 3)
         out["cfg3_fp32_3wavelengths"] = {"workload": w.name, "value": w.voxels / (ms * 1e-3),
                                          "unit": UNIT, "ms_per_call": round(ms, 4),
+                                         "controls_per_s": round(w.mx * w.my / (ms * 1e-3), 1),
                                          "whole_call_hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4)}
         del C, EF, EA, G, E, call
 
@@ -577,9 +579,12 @@ def run_variants(torch, ec, synth, dev, flush_l2,
                 c()
 
         ms_s = _timed(per_region, flush_l2, 20, torch)
+        alg4 = sum(algorithmic_bytes(rw, 1) for rw in regs)
         out["cfg4_batched_64_regions"] = {
             "regions": len(regs), "voxels": vox, "value": vox / (ms_b * 1e-3), "unit": UNIT,
-            "ms_per_call": round(ms_b, 4), "per_region_launches": {
+            "ms_per_call": round(ms_b, 4), "algorithmic_bytes": alg4,
+            "whole_call_hbm_frac": round(alg4 / (ms_b * 1e-3) / 1e9 / peak, 4),
+            "per_region_launches": {
                 "value": vox / (ms_s * 1e-3), "ms_per_call": round(ms_s, 4)},
             "speedup_vs_per_region": round(ms_s / ms_b, 3),
             "default_shapes_ms_per_call": round(ms_default, 4), "autotuned": tuning,

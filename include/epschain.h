@@ -226,6 +226,12 @@ typedef struct {
  * it applies to, or -1 for eps_forward_batched.  Fields: multi 0 or 1,
  * blocks per SM 1 .. 16 (stencil, scatter) and 1 .. 64 (contraction),
  * stage_components 1 or 3, defer_seeds 0 or 1; else EPS_ERR_INVALID_ARG.
+ * The contraction streams the fields of every region through bulk tensor
+ * copies (up to 4 blocks per SM, so larger values act as 4) when the batch
+ * needs at most 192 tensor maps (n * n_lambda * 2); larger batches use
+ * register loads with 4 * contract_blocks_per_sm blocks per SM.  Default
+ * shapes: grouped form, 3 contraction blocks per SM, 3 components staged,
+ * seeds finished in the stencil.
  */
 eps_status_t eps_batched_set_tuning(int32_t n, const eps_problem_t *probs, int32_t n_lambda,
                                    const eps_tuning_t *tuning);

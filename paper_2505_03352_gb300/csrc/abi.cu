@@ -17,6 +17,7 @@
 
 #include "epsc_contract.cuh"
 #include "epsc_contract_tma.cuh"
+#include "epsc_contract_tma_batch.cuh"
 #include "epsc_pack.cuh"
 #include "epsc_launch.h"
 #include "epsc_multi.cuh"
@@ -342,6 +343,60 @@ eps_status_t run_contract_tma(const Geometry &g, int n_lambda, const void *const
                 s);
   }
   return st;
+}
+
+// Arguments of the batched TMA contraction over the regions of `ca`
+// (geometries `gs`, same order); false when the batch or a region's fields
+// or window do not suit it (the register-load contraction then runs).
+bool prepare_contract_tma_batch(const std::vector<const Geometry *> &gs,
+                                const ContractBatchArgs &ca, int n_lambda,
+                                ContractTmaBatchArgs *ta, size_t *smem) {
+  PFN_encodeTiled enc = encode_tiled();
+  if (!enc || n_lambda < 1 || ca.n < 1 || ca.n * n_lambda * 2 > TMA_BATCH_MAX_MAPS) return false;
+  std::memset(ta, 0, sizeof(*ta));
+  long chunks = 0;
+  int bx_max = 0;
+  for (int k = 0; k < ca.n; ++k) {
+    const Geometry &g = *gs[k];
+    const ContractBatchRegion &cr = ca.r[k];
+    int x0 = 0, bx = 0;
+    support_window(g, &x0, &bx);
+    if (bx > TMA_BX_MAX || (g.nz & 1)) return false;
+    ContractTmaBatchRegion &tr = ta->r[k];
+    tr.W = cr.W;
+    tr.ncol = (long)g.nx * g.ny;
+    tr.chunk_start = (int)chunks;
+    tr.k0 = g.k0;
+    tr.nk = g.nk;
+    tr.x0 = x0;
+    tr.bx = bx;
+    tr.map0 = 2 * n_lambda * k;
+    const size_t comp_bytes = (size_t)tr.ncol * g.nz * 8;
+    for (int l = 0; l < n_lambda; ++l) {
+      for (int c = 0; c < 3; ++c) tr.fs[l][c] = cr.fs[l][c];
+      for (int f = 0; f < 2; ++f) {
+        // (2 nz floats) x (columns) x (3 components)
+        cuuint64_t dims[3] = {(cuuint64_t)(2 * g.nz), (cuuint64_t)tr.ncol, 3};
+        cuuint64_t strides[2] = {(cuuint64_t)g.nz * 8, (cuuint64_t)comp_bytes};
+        cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)TMA_BY, 3};
+        cuuint32_t es[3] = {1, 1, 1};
+        if (enc(&ta->maps[tr.map0 + 2 * l + f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                (void *)(f == 0 ? cr.EF[l] : cr.EA[l]), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+          return false;
+      }
+    }
+    chunks += (tr.ncol + TMA_BY - 1) / TMA_BY;
+    bx_max = std::max(bx_max, bx);
+  }
+  if (chunks <= 0 || chunks > (1l << 30)) return false;
+  ta->n = ca.n;
+  ta->nlambda = n_lambda;
+  ta->nchunks = (int)chunks;
+  ta->stage_floats = 6 * TMA_BY * bx_max;
+  *smem = (size_t)TMA_NSTAGE * ta->stage_floats * 4 + 128;
+  return true;
 }
 
 // Packed planes per column (multiple of 4) and bytes of one packed field.
@@ -792,14 +847,19 @@ struct BatchTuning {
   int multi;          // 1: multi form, 0: grouped form
   int fwd_bps;        // persistent stencil blocks per SM (multi form)
   int bwd_bps;        // persistent scatter blocks per SM (multi form)
-  int contract_bps;   // batched contraction blocks per SM
+  int contract_bps;   // batched contraction blocks per SM (TMA form; 4x for register loads)
   int stage_comps;    // eps_hat components staged per round of bulk stores (1 or 3)
   int defer_seeds;    // 1: stencil writes seed factors, the seeds kernel applies W
 };
 // Default: the grouped form, measured faster on the 64-region batch (radius
 // classes 2 .. 8): one kernel holding all twelve radius bodies runs them side
-// by side on an SM and lost to per-class launches there.
-constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 8, 3, 0};
+// by side on an SM and lost to per-class launches there.  Three TMA
+// contraction blocks per SM streamed that batch's fields in 304 us against
+// 368 us with two.
+constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 3, 3, 0};
+// The TMA contraction's ring (2 stages of up to 6 x 32 x 64 floats) leaves
+// room for at most this many blocks per SM.
+constexpr int TMA_BATCH_MAX_BPS = 4;
 
 std::mutex g_tune_mu;
 std::vector<std::pair<uint64_t, BatchTuning>> g_tune;   // small: one entry per tuned batch
@@ -1091,6 +1151,7 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
   std::memset(sa, 0, sizeof(*sa));
   std::vector<FwdRegion> fr(n);
   std::vector<BwdRegion> br(n);
+  std::vector<const Geometry *> gs;
   long ncol = 0;
   for (int k = 0; k < n; ++k) {
     std::memset(&fr[k], 0, sizeof(FwdRegion));
@@ -1108,6 +1169,7 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
     float *seeds = (float *)(base + L.seeds);
     float *pd4 = (float *)(base + L.pd4);
     float *ie2 = (float *)(base + L.ie2);
+    gs.push_back(&rs[k].g);
     ContractBatchRegion &cr = ca->r[ca->n++];
     cr.col_start = ncol;
     cr.nz = g.nz;
@@ -1157,10 +1219,21 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
   if (ncol > 0) {
     int nsm = 0;
     if ((st = sm_count(&nsm)) != EPS_OK) return st;
-    const long per_block = (NTHREADS / 32) * 4;
-    const long blocks = std::max<long>(
-        1, std::min<long>((ncol + per_block - 1) / per_block, (long)nsm * t.contract_bps));
-    st = launch("eps_batched_contract", contract_batched_entry(), dim3((unsigned)blocks), 0, ca, s);
+    std::unique_ptr<ContractTmaBatchArgs> ta(new ContractTmaBatchArgs);
+    size_t tsmem = 0;
+    if (prepare_contract_tma_batch(gs, *ca, n_lambda, ta.get(), &tsmem)) {
+      ta->err = err;
+      const int bps = std::max(1, std::min(t.contract_bps, TMA_BATCH_MAX_BPS));
+      const long blocks = std::max<long>(1, std::min<long>(ta->nchunks, (long)nsm * bps));
+      st = launch("eps_batched_contract", contract_tma_batch_entry(ta->n * ta->nlambda * 2),
+                  dim3((unsigned)blocks), tsmem, ta.get(), s);
+    } else {
+      const long per_block = (NTHREADS / 32) * 4;
+      const long blocks = std::max<long>(
+          1, std::min<long>((ncol + per_block - 1) / per_block, (long)nsm * 4 * t.contract_bps));
+      st = launch("eps_batched_contract", contract_batched_entry(), dim3((unsigned)blocks), 0, ca,
+                  s);
+    }
   }
   if (st != EPS_OK) return st;
   bool any_eps = false;
@@ -1282,7 +1355,7 @@ eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const f
   for (int sweep = 0; sweep < 2 && st == EPS_OK; ++sweep) {
     for (int param = 0; param < 6 && st == EPS_OK; ++param) {
       static const int values[6][4] = {{0, 1, -1, -1}, {1, 3, -1, -1}, {1, 2, 3, 4},
-                                       {1, 2, 3, 4}, {2, 4, 8, 16}, {0, 1, -1, -1}};
+                                       {1, 2, 3, 4}, {1, 2, 3, 4}, {0, 1, -1, -1}};
       for (int v = 0; v < 4 && st == EPS_OK; ++v) {
         const int val = values[param][v];
         if (val < 0) continue;

@@ -26,6 +26,9 @@ const void *contract_batched_entry();
 // Contraction kernel fed by bulk tensor copies (complex64 fields), with room
 // for at least n_lambda wavelengths' tensor maps.
 const void *contract_tma_entry(int n_lambda);
+// Contraction over many regions fed by bulk tensor copies, with room for at
+// least nmaps tensor maps (2 per region and wavelength).
+const void *contract_tma_batch_entry(int nmaps);
 
 // Reduced-precision field path.
 const void *pack_amax_entry();

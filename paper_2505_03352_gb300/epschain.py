@@ -400,7 +400,7 @@ class BatchedVjp:
         defer_seeds (defaults: the library's default shapes)."""
         r = eps_tuning_t()
         base = dict(multi=0, stencil_blocks_per_sm=3, scatter_blocks_per_sm=3,
-                    contract_blocks_per_sm=8, stage_components=3, defer_seeds=0)
+                    contract_blocks_per_sm=3, stage_components=3, defer_seeds=0)
         base.update(shapes)
         for k, v in base.items():
             setattr(r, k, int(v))

@@ -189,3 +189,51 @@ def test_bad_tuning_is_rejected():
                 dict(defer_seeds=5), dict(contract_blocks_per_sm=65)):
         with pytest.raises(ec.EpsError):
             bv.set_tuning(**bad)
+
+
+def test_batched_tma_contraction_is_bitwise_the_per_region_calls():
+    # the batched contraction streams every region through bulk tensor copies
+    # with the single-region kernel's lane order, and the stencil and scatter
+    # run the same tile code: dJ/dC and eps_hat equal the per-region calls bit
+    # for bit (regions of uneven size, slab position, nz and wavelengths)
+    import paper_2505_03352_gb300 as ec
+    import torch
+    regs = region_set(n=16, seed=51)
+    regs[2]["nz"], regs[7]["nz"] = 32, 20
+    for nl in (1, 3):
+        probs, Cs, EF, EA, _ = inputs(regs)
+        if nl > 1:
+            EF = [[e[0]] + [torch.randn_like(e[0]) for _ in range(nl - 1)] for e in EF]
+            EA = [[e[0]] + [torch.randn_like(e[0]) for _ in range(nl - 1)] for e in EA]
+        bv = ec.BatchedVjp(probs, Cs, EF, EA)
+        G, E = bv()
+        ec.eps_sync_status()
+        for k, p in enumerate(probs):
+            g1, e1 = ec.eps_vjp(p, Cs[k], EF[k], EA[k], eps_out=True)
+            ec.eps_sync_status()
+            np.testing.assert_array_equal(E[k].cpu().numpy(), e1.cpu().numpy())
+            np.testing.assert_array_equal(G[k].cpu().numpy(), g1.cpu().numpy())
+
+
+def test_register_load_contraction_for_batches_beyond_the_tensor_map_capacity():
+    # 40 regions x 3 wavelengths need 240 tensor maps, more than one launch
+    # carries: the register-load contraction runs, within rounding of the
+    # per-region calls and within the oracle tolerance
+    import paper_2505_03352_gb300 as ec
+    import torch
+    regs = region_set(n=40, seed=53)
+    probs, Cs, EF, EA, raw = inputs(regs)
+    EF = [[e[0]] + [torch.randn_like(e[0]) for _ in range(2)] for e in EF]
+    EA = [[e[0]] + [torch.randn_like(e[0]) for _ in range(2)] for e in EA]
+    G, E = ec.BatchedVjp(probs, Cs, EF, EA)()
+    ec.eps_sync_status()
+    for k in (0, 13, 39):
+        p = probs[k]
+        g1, e1 = ec.eps_vjp(p, Cs[k], EF[k], EA[k], eps_out=True)
+        ec.eps_sync_status()
+        np.testing.assert_array_equal(E[k].cpu().numpy(), e1.cpu().numpy())
+        assert np.max(np.abs(G[k].cpu().numpy() - g1.cpu().numpy())) <= 1e-5 * g1.abs().max().item()
+        C = raw[k][0]
+        o = orc.Problem(mx=p.mx, my=p.my, nz=p.nz, radius=p.radius, beta=p.beta, bc=p.bc)
+        ref = orc.vjp_fields(o, C, [e.cpu().numpy() for e in EF[k]], [e.cpu().numpy() for e in EA[k]])
+        assert np.max(np.abs(G[k].cpu().numpy() - ref)) <= 1e-4 * np.max(np.abs(ref))
