@@ -415,6 +415,18 @@ eps_status_t eps_opt_step(const eps_problem_t *prob, const eps_morph_t *morph, c
 eps_status_t eps_sync_status(eps_stream_t stream);
 
 /*
+ * Self-test of the device-side timeout path.  Launches one block that
+ * waits, with the same bounded mbarrier wait the contraction kernels use,
+ * on a barrier nothing arrives at, giving up after `cycles` SM clock cycles
+ * (1 .. 2^31; the kernels' own limit is 2^31, about one second).  The block
+ * then records EPS_ERR_DEVICE_TIMEOUT in the device error flag and returns:
+ * no fault, trap or hang, and the context stays usable.  The next
+ * eps_sync_status(stream) reports the timeout and clears it.  Out-of-range
+ * `cycles`: EPS_ERR_INVALID_ARG before any launch.
+ */
+eps_status_t eps_selftest_timeout(int64_t cycles, eps_stream_t stream);
+
+/*
  * eps_vjp without a caller workspace.  The paper has no counterpart: this
  * is for host programs that cannot allocate device memory where they need
  * the gradient (a framework pool that already holds the whole device, or a

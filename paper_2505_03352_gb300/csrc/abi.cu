@@ -773,6 +773,16 @@ eps_status_t eps_sync_status(eps_stream_t stream) {
   return (flag & ERRFLAG_TIMEOUT) ? EPS_ERR_DEVICE_TIMEOUT : EPS_ERR_DEVICE_BOUNDS;
 }
 
+eps_status_t eps_selftest_timeout(int64_t cycles, eps_stream_t stream) {
+  if (cycles < 1 || cycles > (1ll << 31)) return EPS_ERR_INVALID_ARG;
+  SelftestArgs a;
+  eps_status_t st = error_flag_ptr(&a.err);
+  if (st != EPS_OK) return st;
+  a.cycles = (long long)cycles;
+  return launch("eps_selftest_timeout", selftest_timeout_entry(), dim3(1), 0, &a,
+                (cudaStream_t)stream);
+}
+
 eps_status_t eps_set_l2_fetch_granularity(int32_t bytes, int32_t *previous) {
   if (bytes < 0 || bytes > 128) return EPS_ERR_INVALID_ARG;
   size_t old = 0;

@@ -69,12 +69,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait on a phase of an mbarrier: about one second of SM clock.
-// Each try suspends the thread for up to 20 us (hint) instead of spinning.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+// Bounded wait on a phase of an mbarrier: `limit` SM clock cycles (by
+// default 2^31, about one second).  Each try suspends the thread for up to
+// 20 us (hint) instead of spinning.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity,
+                                                  long long limit = 1ll << 31) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }

@@ -29,6 +29,12 @@ const void *contract_tma_entry(int n_lambda);
 // Contraction over many regions fed by bulk tensor copies, with room for at
 // least nmaps tensor maps (2 per region and wavelength).
 const void *contract_tma_batch_entry(int nmaps);
+// One block that waits (bounded) on a barrier nothing arrives at.
+struct SelftestArgs {
+  int *err;
+  long long cycles;
+};
+const void *selftest_timeout_entry();
 
 // Reduced-precision field path.
 const void *pack_amax_entry();

@@ -112,6 +112,7 @@ _PROTOS = {
                                       ctypes.c_size_t, _VP]),
     "eps_profile_start": (ctypes.c_int, []),
     "eps_set_l2_fetch_granularity": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "eps_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
     "eps_profile_stop": (ctypes.c_int, [ctypes.POINTER(eps_profile_entry_t), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]),
     "eps_morph_workspace_size": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, ctypes.c_int32,
@@ -427,6 +428,13 @@ class eps_tuning_t(ctypes.Structure):
 
 def eps_sync_status(stream=None):
     _check(lib().eps_sync_status(_stream(stream)), "eps_sync_status")
+
+
+def eps_selftest_timeout(cycles: int, stream=None):
+    """Launch the device-side timeout self-test (a bounded wait on a barrier
+    nothing arrives at, `cycles` SM clock cycles long); the next
+    eps_sync_status reports EPS_ERR_DEVICE_TIMEOUT."""
+    _check(lib().eps_selftest_timeout(int(cycles), _stream(stream)), "eps_selftest_timeout")
 
 
 def eps_set_l2_fetch_granularity(nbytes: int) -> int:

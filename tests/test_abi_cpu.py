@@ -273,3 +273,9 @@ def test_coarse_workspace_and_validation(L):
     arr = (ctypes.c_void_p * 1)(fake)
     assert L.eps_vjp_coarse(P, G, fake, 1, 0, arr, arr, None, -2.0, fake, None, fake, 64, None) == 3
     assert L.eps_vjp_real_coarse(P, G, fake, None, fake, fake, 1 << 30, None) == 1
+
+
+def test_timeout_selftest_rejects_bad_limits_on_host(L):
+    assert L.eps_selftest_timeout(0, None) == 1            # EPS_ERR_INVALID_ARG
+    assert L.eps_selftest_timeout((1 << 31) + 1, None) == 1
+    assert L.eps_selftest_timeout(-5, None) == 1
