@@ -50,7 +50,7 @@ typedef enum {
   EPS_ERR_UNSUPPORTED = 4,   /* valid request outside what is built (sub != 2, radius > max) */
   EPS_ERR_CUDA = 5,          /* a CUDA runtime call failed */
   EPS_ERR_DEVICE_TIMEOUT = 6,/* a bounded device-side wait gave up */
-  EPS_ERR_DEVICE_BOUNDS = 7  /* a device-side bounds check fired (debug builds) */
+  EPS_ERR_DEVICE_BOUNDS = 7  /* a device-side bounds check fired (debug-bounds builds) */
 } eps_status_t;
 
 typedef enum { EPS_BC_CLAMP = 0, EPS_BC_PERIODIC = 1 } eps_bc_t;
@@ -425,6 +425,20 @@ eps_status_t eps_sync_status(eps_stream_t stream);
  * `cycles`: EPS_ERR_INVALID_ARG before any launch.
  */
 eps_status_t eps_selftest_timeout(int64_t cycles, eps_stream_t stream);
+
+/*
+ * Debug bounds checks.  A library built with -DEPS_DEBUG_BOUNDS
+ * (libepschain_debug.so, `build_lib --debug-bounds`) tests the index of
+ * every global load and store of its kernels that is not bounded by its
+ * own loop (staging gathers, stores, the register-load field reads; TMA
+ * copies are bounded by their tensor maps) against the extent of its
+ * buffer; an index outside records EPS_ERR_DEVICE_BOUNDS in the device
+ * error flag and the access is skipped (a load reads zero).  Nothing traps.
+ * eps_selftest_bounds launches one thread whose check fails without
+ * touching memory, so eps_sync_status then reports EPS_ERR_DEVICE_BOUNDS;
+ * in a release build it returns EPS_ERR_UNSUPPORTED.
+ */
+eps_status_t eps_selftest_bounds(eps_stream_t stream);
 
 /*
  * eps_vjp without a caller workspace.  The paper has no counterpart: this

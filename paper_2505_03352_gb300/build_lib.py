@@ -2,7 +2,11 @@
 
 Each .cu under csrc/ is compiled to an object in parallel, then the objects
 are linked into paper_2505_03352_gb300/libepschain.so (static CUDA runtime).
-Usage:  python -m paper_2505_03352_gb300.build_lib [--force] [-v]
+With debug_bounds (--debug-bounds) the same sources are compiled with
+-DEPS_DEBUG_BOUNDS into libepschain_debug.so (objects under _build_debug/):
+every checked global access then tests its index and records
+EPS_ERR_DEVICE_BOUNDS instead of going out of range.
+Usage:  python -m paper_2505_03352_gb300.build_lib [--force] [-v] [--debug-bounds]
 """
 
 from __future__ import annotations
@@ -21,6 +25,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libepschain.so")
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libepschain_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -46,13 +52,15 @@ def _stale(target, sources):
     return any(os.path.getmtime(s) > t for s in sources)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), debug_bounds: bool = False) -> str:
+    build_dir, lib_path = (BUILD_DEBUG, LIB_DEBUG) if debug_bounds else (BUILD, LIB)
+    extra = list(extra) + (["-DEPS_DEBUG_BOUNDS"] if debug_bounds else [])
+    os.makedirs(build_dir, exist_ok=True)
     cu = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = _deps()
     jobs = []
     for src in cu:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + deps):
             cmd = [nvcc()] + ARCH + CFLAGS + list(extra) + ["-c", src, "-o", obj]
             jobs.append((src, cmd))
@@ -71,15 +79,15 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                     print(out, flush=True)
                 if rc != 0:
                     raise RuntimeError(f"nvcc failed on {src}:\n{out}")
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in cu]
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in cu]
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + ".tmp"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError("link failed:\n" + p.stdout + p.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 def main(argv=None):
@@ -87,9 +95,12 @@ def main(argv=None):
     ap.add_argument("--force", action="store_true")
     ap.add_argument("-v", "--verbose", action="store_true")
     ap.add_argument("--ptxas-v", action="store_true", help="print register/smem usage")
+    ap.add_argument("--debug-bounds", action="store_true",
+                    help="build libepschain_debug.so with device-side bounds checks")
     a = ap.parse_args(argv)
     extra = ["-Xptxas", "-v"] if a.ptxas_v else []
-    print(build(force=a.force or a.ptxas_v, verbose=a.verbose or a.ptxas_v, extra=extra))
+    print(build(force=a.force or a.ptxas_v, verbose=a.verbose or a.ptxas_v, extra=extra,
+                debug_bounds=a.debug_bounds))
 
 
 if __name__ == "__main__":

@@ -406,7 +406,7 @@ size_t packed_bytes(const Geometry &g) {
 }
 
 eps_status_t run_contract_packed(const Geometry &g, int n_lambda, int type, const void *const *EF,
-                                 const void *const *EA, const float (*fs)[3], float *Wm,
+                                 const void *const *EA, const float (*fs)[3], float *Wm, int *err,
                                  cudaStream_t s) {
   ContractPackedArgs pa;
   std::memset(&pa, 0, sizeof(pa));
@@ -423,6 +423,7 @@ eps_status_t run_contract_packed(const Geometry &g, int n_lambda, int type, cons
     for (int c = 0; c < 3; ++c) pa.fs[l][c] = fs[l][c];
   }
   pa.W = Wm;
+  pa.err = err;
   int nsm = 0;
   eps_status_t st = sm_count(&nsm);
   if (st != EPS_OK) return st;
@@ -467,12 +468,14 @@ eps_status_t stencil_form(const Geometry &g, StencilForm *f, long *blocks) {
   return EPS_OK;
 }
 
-eps_status_t run_seeds_one(const Geometry &g, const float *W, float *seeds, cudaStream_t s) {
+eps_status_t run_seeds_one(const Geometry &g, const float *W, float *seeds, int *err,
+                           cudaStream_t s) {
   SeedsArgs sa;
   std::memset(&sa, 0, sizeof(sa));
   sa.n = 1;
   sa.ncol = (long)g.nx * g.ny;
   sa.r[0] = SeedsRegion{0, sa.ncol, W, seeds};
+  sa.err = err;
   return run_seeds(sa, s);
 }
 
@@ -617,6 +620,7 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   ca.nk = r.g.nk;
   ca.nlambda = n_lambda;
   ca.mode = MODE_C64;
+  ca.err = err;
   ca.W = Wm;
   bool sector_ok = (r.g.nz & 3) == 0;
   for (int l = 0; l < n_lambda; ++l) {
@@ -634,7 +638,7 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
                         : EPS_ERR_UNSUPPORTED;
     if (st == EPS_ERR_UNSUPPORTED) st = run_contract(ca, sector_ok ? 4 : 8, s);
   } else {
-    st = run_contract_packed(r.g, n_lambda, field_type, EF, EA, ca.fs, Wm, s);
+    st = run_contract_packed(r.g, n_lambda, field_type, EF, EA, ca.fs, Wm, err, s);
   }
   if (st != EPS_OK) return st;
 
@@ -659,7 +663,7 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
               smem, &fa, s, true);
   if (st != EPS_OK) return st;
   // 3. (seeds-kernel form) seeds = factor * W, once both grids are done
-  if (form.defer == 1 && (st = run_seeds_one(r.g, Wm, seeds, s)) != EPS_OK) return st;
+  if (form.defer == 1 && (st = run_seeds_one(r.g, Wm, seeds, err, s)) != EPS_OK) return st;
   // 4. transposes down to dJ/dC
   return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
 }
@@ -690,6 +694,7 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
   ca.k0 = r.g.k0;
   ca.nk = r.g.nk;
   ca.mode = MODE_REAL;
+  ca.err = err;
   ca.G = G;
   ca.W = Wm;
   if ((st = run_contract(ca, 8, s)) != EPS_OK) return st;
@@ -708,7 +713,7 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
   const size_t smem = fwd_smem(kf, r.g, 0, &fa.r.stage_floats);
   st = launch("eps_vjp_real_stencil", kf.fn, dim3((unsigned)blocks), smem, &fa, s, true);
   if (st != EPS_OK) return st;
-  if (form.defer == 1 && (st = run_seeds_one(r.g, Wm, seeds, s)) != EPS_OK) return st;
+  if (form.defer == 1 && (st = run_seeds_one(r.g, Wm, seeds, err, s)) != EPS_OK) return st;
   return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
 }
 
@@ -747,6 +752,7 @@ eps_status_t eps_field_pack(const eps_problem_t *prob, int32_t field_type, const
   pa.type = field_type;
   pa.src = (const float2 *)src;
   pa.dst = (unsigned char *)dst;
+  if ((st = error_flag_ptr(&pa.err)) != EPS_OK) return st;
   int nsm = 0;
   if ((st = sm_count(&nsm)) != EPS_OK) return st;
   if (cudaMemsetAsync(dst, 0, 16, s) != cudaSuccess) return EPS_ERR_CUDA;
@@ -781,6 +787,20 @@ eps_status_t eps_selftest_timeout(int64_t cycles, eps_stream_t stream) {
   a.cycles = (long long)cycles;
   return launch("eps_selftest_timeout", selftest_timeout_entry(), dim3(1), 0, &a,
                 (cudaStream_t)stream);
+}
+
+eps_status_t eps_selftest_bounds(eps_stream_t stream) {
+#ifdef EPS_DEBUG_BOUNDS
+  SelftestArgs a;
+  eps_status_t st = error_flag_ptr(&a.err);
+  if (st != EPS_OK) return st;
+  a.cycles = 0;
+  return launch("eps_selftest_bounds", selftest_bounds_entry(), dim3(1), 0, &a,
+                (cudaStream_t)stream);
+#else
+  (void)stream;
+  return EPS_ERR_UNSUPPORTED;
+#endif
 }
 
 eps_status_t eps_set_l2_fetch_granularity(int32_t bytes, int32_t *previous) {
@@ -1225,7 +1245,9 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
     br[k].dJdC = dJdC[k];
   }
   ca->ncol = ncol;
+  ca->err = err;
   sa->ncol = ncol;
+  sa->err = err;
   if (ncol > 0) {
     int nsm = 0;
     if ((st = sm_count(&nsm)) != EPS_OK) return st;
@@ -1445,5 +1467,7 @@ eps_status_t subpixel_factor_offset(const eps_problem_t *prob, size_t *offset, s
 }
 
 eps_status_t sm_count_current(int *n) { return sm_count(n); }
+
+eps_status_t error_flag(int **flag) { return error_flag_ptr(flag); }
 
 }  // namespace epsc_host

@@ -60,6 +60,7 @@ eps_status_t run_expand(const eps_problem_t *prob, const eps_coarse_t *cg, const
   CoarseArgs a = args_of(prob, cg);
   a.c = c;
   a.phi = phi;
+  if ((st = epsc_host::error_flag(&a.err)) != EPS_OK) return st;
   const long n = (long)prob->mx * prob->my;
   const long blocks = std::max<long>(1, std::min<long>((n + NTHREADS - 1) / NTHREADS, (long)nsm * 8));
   return epsc_host::launch_kernel("eps_coarse_expand", (const void *)&coarse_expand_kernel,
@@ -71,6 +72,8 @@ eps_status_t run_transpose(const eps_problem_t *prob, const eps_coarse_t *cg, co
   CoarseArgs a = args_of(prob, cg);
   a.g = g;
   a.dc = dc;
+  eps_status_t st = epsc_host::error_flag(&a.err);
+  if (st != EPS_OK) return st;
   const long blocks = (long)cg->ncx * cg->ncy;   // one block per node
   if (blocks > 0x7fffffffL) return EPS_ERR_SHAPE;
   return epsc_host::launch_kernel("eps_coarse_transpose", (const void *)&coarse_transpose_kernel,

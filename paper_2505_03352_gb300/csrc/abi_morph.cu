@@ -110,6 +110,8 @@ eps_status_t run_map(const char *name, int kind, int rp1, const float *w, const 
   ma.aux2 = aux2;
   ma.out = out;
   ma.out2 = out2;
+  eps_status_t st = epsc_host::error_flag(&ma.err);
+  if (st != EPS_OK) return st;
   std::memcpy(ma.w, w, sizeof(ma.w));
   const KernelEntry k = map_entry(rp1, prob->bc, kind);
   const dim3 grid((prob->my + MT_B - 1) / MT_B, (prob->mx + MT_A - 1) / MT_A);

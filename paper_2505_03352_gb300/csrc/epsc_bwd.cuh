@@ -115,8 +115,9 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
     const size_t rowo = row_ok ? (size_t)(clamp ? va : wrapi(va, g.mx)) * g.my : 0;
     for (int c = tx; c < DB; c += 32) {
       const int vb = db_lo + c;
-      const bool ok = row_ok && (!clamp || (vb >= 0 && vb < g.my));
-      const size_t o = ok ? rowo + (clamp ? vb : wrapi(vb, g.my)) : 0;
+      bool ok = row_ok && (!clamp || (vb >= 0 && vb < g.my));
+      size_t o = ok ? rowo + (clamp ? vb : wrapi(vb, g.my)) : 0;
+      if (!EPSC_IN_BOUNDS(o, 1, (size_t)g.mx * g.my, a.err)) ok = false, o = 0;
       cp_async4(sU + r * DBP + c, rg.pd4 + o, ok);
       cp_async4(sIE2 + r * DBP + c, rg.ie2 + o, ok);
     }
@@ -127,8 +128,9 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
     const size_t rowo = row_ok ? (size_t)(clamp ? vi : wrapi(vi, g.nx)) * g.ny : 0;
     for (int c = tx; c < NCJ; c += 32) {
       const int vj = cj_lo + c;
-      const bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
-      const size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
+      bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
+      size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
+      if (!EPSC_IN_BOUNDS(o, 1, plane, a.err)) ok = false, o = 0;
       float *d = sSeed + r * S::NCJ + c;
       cp_async4(d + 0 * S::NC, rg.seeds + S_DAX * plane + o, ok);
       cp_async4(d + 1 * S::NC, rg.seeds + S_DHX * plane + o, ok);
@@ -144,8 +146,9 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
     const size_t rowo = row_ok ? (size_t)(clamp ? vi : wrapi(vi, g.nx)) * g.ny : 0;
     for (int c = tx; c < NCJ + 2; c += 32) {
       const int vj = cj_lo - 1 + c;
-      const bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
-      const size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
+      bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
+      size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
+      if (!EPSC_IN_BOUNDS(o, 1, plane, a.err)) ok = false, o = 0;
       float *d = sG + r * S::NGJ + c;
       cp_async4(d + 0 * S::NG, rg.seeds + S_GXX * plane + o, ok);
       cp_async4(d + 1 * S::NG, rg.seeds + S_GYX * plane + o, ok);
@@ -253,7 +256,8 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
       float acc = 0.f;
       for (int x = ra0; x <= ra1; ++x)
         for (int y = rb0; y <= rb1; ++y) acc += sdc[x * S::GB_MAX + y];
-      rg.dJdC[(size_t)ga * g.my + gb] = acc;
+      const size_t go = (size_t)ga * g.my + gb;
+      if (EPSC_IN_BOUNDS(go, 1, (size_t)g.mx * g.my, a.err)) rg.dJdC[go] = acc;
     }
   }
 }

@@ -21,6 +21,7 @@ struct CoarseArgs {
   float *phi;         // [mx][my]
   const float *g;     // [mx][my]  (transpose)
   float *dc;          // [ncx][ncy] (transpose)
+  int *err;           // error flag (debug bounds checks)
 };
 
 // Subpixel a's centre in node units is s = (a + 1/2) / h = (2a + 1)(nc - 1) / (2m):
@@ -51,6 +52,9 @@ __global__ void __launch_bounds__(NTHREADS) coarse_expand_kernel(const __grid_co
     float tx, ty;
     hat_pair(xa, a.mx, a.ncx, i0, tx);
     hat_pair(yb, a.my, a.ncy, j0, ty);
+    // nodes (i0, j0) .. (i0 + 1, j0 + 1)
+    if (!EPSC_IN_BOUNDS((size_t)i0 * a.ncy + j0, (size_t)a.ncy + 2, (size_t)a.ncx * a.ncy, a.err))
+      continue;
     const float *c0 = a.c + (size_t)i0 * a.ncy + j0;
     const float *c1 = c0 + a.ncy;
     const float lo = fmaf(ty, __ldg(c0 + 1), (1.f - ty) * __ldg(c0));
@@ -79,6 +83,8 @@ __global__ void __launch_bounds__(NTHREADS) coarse_transpose_kernel(const __grid
   for (int xa = a_lo + warp; xa <= a_hi; xa += NTHREADS / 32) {
     const float wx = hat_w(xa, i, a.mx, a.ncx);
     if (wx == 0.f) continue;
+    if (!EPSC_IN_BOUNDS((size_t)xa * a.my + b_lo, b_hi - b_lo + 1, (size_t)a.mx * a.my, a.err))
+      continue;
     const float *row = a.g + (size_t)xa * a.my;
     float racc = 0.f;
     for (int yb = b_lo + lane; yb <= b_hi; yb += 32) racc = fmaf(hat_w(yb, j, a.my, a.ncy), __ldg(row + yb), racc);

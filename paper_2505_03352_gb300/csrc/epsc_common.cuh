@@ -41,6 +41,23 @@ enum Mode : int { MODE_FWD = 0, MODE_C64 = 1, MODE_REAL = 2 };
 constexpr int ERRFLAG_TIMEOUT = 1;   // a bounded wait gave up
 constexpr int ERRFLAG_BOUNDS = 2;    // a bounds check fired
 
+// Debug bounds checks.  Built with -DEPS_DEBUG_BOUNDS, EPSC_IN_BOUNDS(lo,
+// cnt, n, err) tests that elements [lo, lo + cnt) lie inside a buffer of n
+// elements (lo is taken as unsigned, so a negative index fails); a failure
+// sets ERRFLAG_BOUNDS in *err and the caller skips the access (a load
+// reads zero).  Release builds compile every check to `true`.
+#ifdef EPS_DEBUG_BOUNDS
+__device__ __forceinline__ bool dbg_in_bounds(size_t lo, size_t cnt, size_t n, int *err) {
+  if (lo <= n && cnt <= n - lo) return true;
+  if (err) atomicOr(err, ERRFLAG_BOUNDS);
+  return false;
+}
+#define EPSC_IN_BOUNDS(lo, cnt, n, err) \
+  ::epsc::dbg_in_bounds((size_t)(lo), (size_t)(cnt), (size_t)(n), (err))
+#else
+#define EPSC_IN_BOUNDS(lo, cnt, n, err) true
+#endif
+
 // seed planes, [NSEED][nx][ny]: the stencil writes W-independent factors,
 // the seeds kernel multiplies them by the column's Eq. 1 sums
 enum Seed : int {
@@ -84,6 +101,7 @@ struct SeedsRegion {
 struct SeedsArgs {
   int n;
   long ncol;
+  int *err;                      // error flag (debug bounds checks)
   SeedsRegion r[EPS_MAX_BATCH];
 };
 

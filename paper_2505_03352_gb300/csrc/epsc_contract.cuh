@@ -27,6 +27,7 @@ struct ContractArgs {
   float fs[EPS_MAX_LAMBDA][3];   // scale * s_F * s_A per wavelength and component
   const float *G;                // MODE_REAL cotangent
   float *W;                      // [4][nx][ny]
+  int *err;                      // error flag (debug bounds checks)
 };
 
 struct F8 {
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(NTHREADS) contract_kernel(const __grid_constan
             const long col = base + u;
             if (col >= ncol) break;
             const size_t off = (size_t)col * a.nz * 2 + (size_t)k * 2;
+            if (!EPSC_IN_BOUNDS(off, 2 * PL, cstride, a.err)) continue;
             float re[3][PL];
             if (L == 4) {
               F8 f[3], e[3];
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__(NTHREADS) contract_kernel(const __grid_constan
         if (col >= ncol) break;
         const float *gc = a.G + (size_t)col * a.nz;
         for (int k = klo + gl; k <= khi; k += L) {
+          if (!EPSC_IN_BOUNDS((size_t)col * a.nz + k, 1, gs, a.err)) continue;
           const float gx = __ldg(gc + k), gy = __ldg(gc + gs + k), gz = __ldg(gc + 2 * gs + k);
           const bool in_xy = k >= klo + 1;
           acc[u][0] += in_xy ? gx : 0.f;
@@ -187,6 +190,7 @@ struct ContractBatchRegion {
 struct ContractBatchArgs {
   int n;
   long ncol;                              // total columns over all regions
+  int *err;                               // error flag (debug bounds checks)
   ContractBatchRegion r[EPS_MAX_BATCH];
 };
 
@@ -215,6 +219,7 @@ __global__ void __launch_bounds__(NTHREADS) contract_batched_kernel(const __grid
         const float *ea = rg.EA[l];
         for (int pc = (klo >> 1) + gl; pc <= (khi >> 1); pc += L) {
           const size_t off = (size_t)lc * rg.nz * 2 + (size_t)pc * 4;
+          if (!EPSC_IN_BOUNDS(off, 4, cstride, a.err)) continue;
           float re0[3], re1[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {

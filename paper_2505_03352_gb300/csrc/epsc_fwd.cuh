@@ -97,7 +97,9 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
     const int c = idx - r * CB;
     const int ga = bc_map_t<BC>(ca0 + r, g.mx);
     const int gb = bc_map_t<BC>(cb0 + c, g.my);
-    cp_async4(sC + idx, rg.C + (size_t)ga * g.my + gb, true);
+    const size_t o = (size_t)ga * g.my + gb;
+    const bool ok = EPSC_IN_BOUNDS(o, 1, (size_t)g.mx * g.my, a.err);
+    cp_async4(sC + idx, rg.C + (ok ? o : 0), ok);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -132,8 +134,10 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
         const int ra = r0 + k - 3, rb = col - 3;   // core subpixel of the tile?
         if (ra >= 0 && ra < 2 * nvi && rb >= 0 && rb < 2 * nvj) {
           const size_t go = (size_t)(2 * i0 + ra) * g.my + 2 * j0 + rb;
-          rg.pd4[go] = 0.5f * g.beta * g.deps * (t * inv * inv);
-          rg.ie2[go] = ie * ie;
+          if (EPSC_IN_BOUNDS(go, 1, (size_t)g.mx * g.my, a.err)) {
+            rg.pd4[go] = 0.5f * g.beta * g.deps * (t * inv * inv);
+            rg.ie2[go] = ie * ie;
+          }
         }
       }
     }
@@ -338,10 +342,13 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
         if (tid == 0) {
           for (int comp = c0; comp <= c1; ++comp) {
             float *base = comp < 3 ? rg.eps + comp * cplane : rg.offdiag + (comp - 3) * cplane;
-            for (int r = 0; r < nvi; ++r)
-              bulk_store(base + ((size_t)(i0 + r) * g.ny + j0) * g.nz,
-                         sbuf + (comp - c0) * comp_floats + r * TJ * g.nz,
-                         (unsigned)(nvj * g.nz * 4));
+            for (int r = 0; r < nvi; ++r) {
+              const size_t off = ((size_t)(i0 + r) * g.ny + j0) * g.nz;
+              if (EPSC_IN_BOUNDS((comp < 3 ? comp : comp - 3) * cplane + off, nvj * g.nz,
+                                 (comp < 3 ? 3 : (rg.normals3d ? 4 : 2)) * cplane, a.err))
+                bulk_store(base + off, sbuf + (comp - c0) * comp_floats + r * TJ * g.nz,
+                           (unsigned)(nvj * g.nz * 4));
+            }
           }
           bulk_commit();
         }
@@ -353,7 +360,11 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
         float *base = comp < 3 ? rg.eps + comp * cplane : rg.offdiag + (comp - 3) * cplane;
         const float vm = comp == 0 ? ex : comp == 1 ? ey : comp == 3 ? odx : comp == 4 ? ody
                          : comp == 5 ? ezx3 : ezy3;
-        float *dst = base + ((size_t)ci * g.ny + cj) * g.nz;
+        const size_t off = ((size_t)ci * g.ny + cj) * g.nz;
+        if (!EPSC_IN_BOUNDS((comp < 3 ? comp : comp - 3) * cplane + off, g.nz,
+                            (comp < 3 ? 3 : (rg.normals3d ? 4 : 2)) * cplane, a.err))
+          continue;
+        float *dst = base + off;
         for (int k = 0; k < g.nz; ++k)
           dst[k] = plane_value(comp, k, g.k0, g.nk, vm, ezi, ezf3, g.eps_clad);
       }
@@ -396,7 +407,7 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
   }
   float Wx = 1.f, Wy = 1.f, Wzi = 0.f, Wzf = 1.f;
   if (!rg.defer_seeds) griddep_wait();   // the contraction grid has completed
-  if (valid) {
+  if (valid && EPSC_IN_BOUNDS((size_t)ci * g.ny + cj, 1, (size_t)g.nx * g.ny, a.err)) {
     const size_t plane = (size_t)g.nx * g.ny;
     if (!rg.defer_seeds) {
       const float *wc = rg.W + (size_t)ci * g.ny + cj;

@@ -38,4 +38,9 @@ eps_status_t morph_base_offset(const eps_problem_t *prob, const eps_morph_t *mor
 // Multiprocessor count of the current device.
 eps_status_t sm_count_current(int *n);
 
+// Device address of the library's error flag on the current device (the
+// flag eps_sync_status reads), for kernels that record timeouts or debug
+// bounds failures.
+eps_status_t error_flag(int **flag);
+
 }  // namespace epsc_host

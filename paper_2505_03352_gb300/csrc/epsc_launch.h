@@ -35,6 +35,8 @@ struct SelftestArgs {
   long long cycles;
 };
 const void *selftest_timeout_entry();
+// One thread whose bounds check fails (debug-bounds builds; no memory access).
+const void *selftest_bounds_entry();
 
 // Reduced-precision field path.
 const void *pack_amax_entry();

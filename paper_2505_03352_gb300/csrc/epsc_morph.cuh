@@ -42,6 +42,7 @@ struct MapArgsN {
   const float *aux2;    // LSE_T: rho_k
   float *out;           // FRONT: rho_0; LSE: rho_{k+1}; LSE_T: g_k; FRONT_T: dJ/dC
   float *out2;          // FRONT: P'(u)
+  int *err;             // error flag (debug bounds checks)
   float w[NW];
 };
 using MapArgs = MapArgsN<MAX_BOX * MAX_BOX>;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(NTHREADS) map_kernel(
         x = bc_map(x, a.mx, BC);
         y = bc_map(y, a.my, BC);
       }
-      if (inside) {
+      if (inside && EPSC_IN_BOUNDS((size_t)x * a.my + y, 1, (size_t)a.mx * a.my, a.err)) {
         const size_t o = (size_t)x * a.my + y;
         if (KIND == MAP_FRONT) {
           v = __ldg(a.in + o);
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(NTHREADS) map_kernel(
         continue;
       }
       const size_t o = (size_t)(ga_lo + r) * a.my + (gb_lo + col);
+      if (!EPSC_IN_BOUNDS(o, 1, (size_t)a.mx * a.my, a.err)) continue;
       if (KIND == MAP_FRONT) {
         // with x = beta (u - eta) and t = exp(-2|x|) <= 1 (no overflow at any
         // beta): rho_0 = 1/(1+t) for x >= 0, t/(1+t) below, and
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(NTHREADS) map_kernel(
     for (int i = ra0; i <= ra1; ++i)
       for (int j = rb0; j <= rb1; ++j) acc += sH[i * S::GB_MAX + j];
     const size_t o = (size_t)x * a.my + y;
+    if (!EPSC_IN_BOUNDS(o, 1, (size_t)a.mx * a.my, a.err)) continue;
     if (KIND == MAP_LSE_T) acc *= expf(a.alpha * (lse_s(__ldg(a.aux2 + o), a.erode) - 1.f));
     a.out[o] = acc;
   }

@@ -25,10 +25,12 @@ constexpr int W_ALL = woff(MAX_RP1 + 1);
 template <int RP1>
 constexpr int WOFF = woff(RP1);
 
-// Weight view of one radius class: `w` points at its box in the parameters.
+// Weight view of one radius class: `w` points at its box in the parameters;
+// `err` is the launch's error flag (debug bounds checks).
 template <int RP1>
 struct WView {
   const float *w;
+  int *err;
 };
 
 struct FwdMultiArgs {
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) fwd_multi_kernel(const __grid_con
     switch (a.rp1[k]) {
 #define EPSC_FWD_CASE(R) \
   case R:                \
-    fwd_tile<R, BC>(WView<R>{a.w + WOFF<R>}, a.r[k], i0, j0); \
+    fwd_tile<R, BC>(WView<R>{a.w + WOFF<R>, a.err}, a.r[k], i0, j0); \
     break;
       EPSC_MULTI_CASES(EPSC_FWD_CASE)
 #undef EPSC_FWD_CASE
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) bwd_multi_kernel(const __grid_con
     switch (a.rp1[k]) {
 #define EPSC_BWD_CASE(R) \
   case R:                \
-    bwd_tile<R, BC>(WView<R>{a.w + WOFF<R>}, a.r[k], a0, b0); \
+    bwd_tile<R, BC>(WView<R>{a.w + WOFF<R>, a.err}, a.r[k], a0, b0); \
     break;
       EPSC_MULTI_CASES(EPSC_BWD_CASE)
 #undef EPSC_BWD_CASE

@@ -28,6 +28,7 @@ struct PackArgs {
   int type;                     // EPS_FIELD_BF16X2_SCALED or EPS_FIELD_F16X2_SCALED
   const float2 *src;            // complex64 [3][nx][ny][nz]
   unsigned char *dst;           // packed buffer
+  int *err;                     // error flag (debug bounds checks)
 };
 
 struct ContractPackedArgs {
@@ -36,6 +37,7 @@ struct ContractPackedArgs {
   const unsigned char *EA[EPS_MAX_LAMBDA];
   float fs[EPS_MAX_LAMBDA][3];   // scale * extra caller factors
   float *W;                      // [4][nx][ny]
+  int *err;                      // error flag (debug bounds checks)
 };
 
 // The kernels below are compiled in one translation unit only.
@@ -52,7 +54,9 @@ __global__ void __launch_bounds__(NTHREADS) pack_amax_kernel(const __grid_consta
   for (long t = (long)blockIdx.x * NTHREADS + threadIdx.x; t < total; t += (long)gridDim.x * NTHREADS) {
     const long col = t / (a.nk + 1);
     const int k = a.k0 + (int)(t - col * (a.nk + 1));
-    const float2 v = a.src[((size_t)c * ncol + col) * a.nz + k];
+    const size_t si = ((size_t)c * ncol + col) * a.nz + k;
+    if (!EPSC_IN_BOUNDS(si, 1, (size_t)3 * ncol * a.nz, a.err)) continue;
+    const float2 v = a.src[si];
     m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
   }
 #pragma unroll
@@ -75,7 +79,8 @@ __global__ void __launch_bounds__(NTHREADS) pack_kernel(const __grid_constant__ 
     const float inv = amax > 0.f ? target / amax : 1.f;
     const int k = a.k0 + kk;
     float2 v = make_float2(0.f, 0.f);
-    if (kk <= a.nk && k < a.nz) v = a.src[(size_t)cc * a.nz + k];
+    if (kk <= a.nk && k < a.nz && EPSC_IN_BOUNDS((size_t)cc * a.nz + k, 1, (size_t)3 * ncol * a.nz, a.err))
+      v = a.src[(size_t)cc * a.nz + k];
     unsigned bits;
     if (a.type == EPS_FIELD_BF16X2_SCALED) {
       const __nv_bfloat162 h = __floats2bfloat162_rn(v.x * inv, v.y * inv);
@@ -125,6 +130,7 @@ __global__ void __launch_bounds__(NTHREADS) contract_packed_kernel(const __grid_
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const size_t base = ((size_t)c * ncol + col) * nq;
+        if (!EPSC_IN_BOUNDS(base, nq, (size_t)3 * ncol * nq, a.err)) continue;
         float s_in = 0.f, s_face = 0.f;
 #pragma unroll 4
         for (int q = 0; q < nq; ++q) {   // unrolled: more loads in flight per thread
@@ -146,16 +152,18 @@ __global__ void __launch_bounds__(NTHREADS) contract_packed_kernel(const __grid_
         }
         const float sc = __ldg(hf + c) * __ldg(ha + c) * a.fs[l][c];
         if (c < 2) {
-          sums[c] = s_in * sc;
+          sums[c] = __fmul_rn(s_in, sc);
         } else {
-          sums[2] = s_in * sc;
-          sums[3] = s_face * sc;
+          sums[2] = __fmul_rn(s_in, sc);
+          sums[3] = __fmul_rn(s_face, sc);
         }
       }
-      wx += sums[0];
-      wy += sums[1];
-      wzi += sums[2];
-      wzf += sums[3];
+      // a rounded product, then a rounded sum: one fixed order whatever the
+      // compiler could fuse
+      wx = __fadd_rn(wx, sums[0]);
+      wy = __fadd_rn(wy, sums[1]);
+      wzi = __fadd_rn(wzi, sums[2]);
+      wzf = __fadd_rn(wzf, sums[3]);
     }
     a.W[0 * ncol + col] = wx;
     a.W[1 * ncol + col] = wy;

@@ -19,6 +19,7 @@ __global__ void __launch_bounds__(NTHREADS) seeds_kernel(const __grid_constant__
     while (k + 1 < a.n && c >= a.r[k + 1].col_start) ++k;
     const SeedsRegion &rg = a.r[k];
     const long j = c - rg.col_start, p = rg.ncol;
+    if (!EPSC_IN_BOUNDS(j, 1, p, a.err)) continue;
     const float Wx = __ldg(rg.W + j), Wy = __ldg(rg.W + p + j);
     const float Wzi = __ldg(rg.W + 2 * p + j), Wzf = __ldg(rg.W + 3 * p + j);
     float *s = rg.seeds + j;

@@ -1,7 +1,7 @@
-// Self-test of the device-side timeout path: one block waits, with the
-// contraction kernels' bounded mbarrier wait, on a barrier nothing arrives
-// at; the wait gives up after `cycles` SM clock cycles, the block records
-// the timeout in the error flag and returns.
+// Self-tests of the device-side error paths.  Timeout: one block waits,
+// with the contraction kernels' bounded mbarrier wait, on a barrier nothing
+// arrives at; the wait gives up after `cycles` SM clock cycles, the block
+// records the timeout in the error flag and returns.
 #include "epsc_contract_tma.cuh"
 #include "epsc_launch.h"
 
@@ -18,5 +18,17 @@ __global__ void __launch_bounds__(NTHREADS) selftest_timeout_kernel(const __grid
 }
 
 const void *selftest_timeout_entry() { return (const void *)&selftest_timeout_kernel; }
+
+// Debug-bounds builds: one thread runs a bounds check that fails (element n
+// of a buffer of n elements) and touches no memory, so the host then reads
+// EPS_ERR_DEVICE_BOUNDS.  In release builds the check compiles away.
+__global__ void __launch_bounds__(NTHREADS) selftest_bounds_kernel(const __grid_constant__ SelftestArgs a) {
+  if (threadIdx.x == 0) {
+    const size_t n = 16;
+    if (!EPSC_IN_BOUNDS(n, 1, n, a.err)) return;
+  }
+}
+
+const void *selftest_bounds_entry() { return (const void *)&selftest_bounds_kernel; }
 
 }  // namespace epsc

@@ -113,6 +113,7 @@ _PROTOS = {
     "eps_profile_start": (ctypes.c_int, []),
     "eps_set_l2_fetch_granularity": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "eps_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
+    "eps_selftest_bounds": (ctypes.c_int, [ctypes.c_void_p]),
     "eps_profile_stop": (ctypes.c_int, [ctypes.POINTER(eps_profile_entry_t), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]),
     "eps_morph_workspace_size": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, ctypes.c_int32,
@@ -435,6 +436,12 @@ def eps_selftest_timeout(cycles: int, stream=None):
     nothing arrives at, `cycles` SM clock cycles long); the next
     eps_sync_status reports EPS_ERR_DEVICE_TIMEOUT."""
     _check(lib().eps_selftest_timeout(int(cycles), _stream(stream)), "eps_selftest_timeout")
+
+
+def eps_selftest_bounds(stream=None):
+    """Launch the debug-bounds self-test (a failing bounds check, no memory
+    access); raises EpsError(EPS_ERR_UNSUPPORTED) on a release build."""
+    _check(lib().eps_selftest_bounds(_stream(stream)), "eps_selftest_bounds")
 
 
 def eps_set_l2_fetch_granularity(nbytes: int) -> int:

@@ -279,3 +279,9 @@ def test_timeout_selftest_rejects_bad_limits_on_host(L):
     assert L.eps_selftest_timeout(0, None) == 1            # EPS_ERR_INVALID_ARG
     assert L.eps_selftest_timeout((1 << 31) + 1, None) == 1
     assert L.eps_selftest_timeout(-5, None) == 1
+
+
+def test_debug_bounds_entry_is_declared_and_exported(L):
+    # a release build answers the bounds self-test with EPS_ERR_UNSUPPORTED
+    # before any launch
+    assert L.eps_selftest_bounds(None) == 4               # EPS_ERR_UNSUPPORTED
