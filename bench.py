@@ -49,9 +49,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=40)
-    ap.add_argument("--variant-set", default="cfg3,cfg4,cfg5,morph,opt,coarse,normals3d",
+    ap.add_argument("--variant-set", default="cfg3,cfg4,cfg5,morph,opt,coarse,normals3d,autograd",
                     help="comma-separated variants to run "
-                         "(cfg3, cfg4, cfg5, morph, opt, coarse, normals3d)")
+                         "(cfg3, cfg4, cfg5, morph, opt, coarse, normals3d, autograd)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the cfg3 / batched cfg4 / reduced-precision cfg5 measurements")
     return ap.parse_args()
@@ -521,7 +521,7 @@ def _window_error(w, C, EF, EA, g_gpu, half=48):
 
 
 def run_variants(torch, ec, synth, dev, flush_l2,
-                 sel=("cfg3", "cfg4", "cfg5", "morph", "opt", "coarse", "normals3d")):
+                 sel=("cfg3", "cfg4", "cfg5", "morph", "opt", "coarse", "normals3d", "autograd")):
     """The differentiation (cfg3), batching (cfg4) and precision (cfg5) forms,
     each timed like the main workload (L2 flushed before every call)."""
     out = {}
@@ -632,7 +632,49 @@ def run_variants(torch, ec, synth, dev, flush_l2,
         out["coarse_controls"] = run_coarse_variant(torch, ec, synth, dev, flush_l2)
     if "normals3d" in sel:
         out["forward_tensor_cfg2"] = run_tensor_variant(torch, ec, synth, dev, flush_l2)
+    if "autograd" in sel:
+        out["autograd_cfg3"] = run_autograd_variant(torch, ec, synth, dev, flush_l2)
     return out
+
+
+def run_autograd_variant(torch, ec, synth, dev, flush_l2):
+    """cfg3 through the torch.autograd.Function (the differentiation form):
+    forward eps_hat = EpsChain(C) (eps_forward), then backward with a real
+    cotangent G [3, nx, ny, nz] (eps_vjp_real), which recomputes the filtered
+    density and projection from C.  Algorithmic bytes per Yee column: C read
+    twice (16 B each), eps_hat written (12 nz), G read on its 3 nk + 1
+    support planes (4 B each) and dJ/dC written (16 B)."""
+    import numpy as np
+    w = synth.WORKLOADS[3]
+    p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+    Cp = torch.from_numpy(synth.controls(w)).to(dev).requires_grad_(True)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3303)
+    G = torch.randn((3, w.nx, w.ny, w.nz), generator=gen, device=dev)
+
+    def step():
+        Cp.grad = None
+        eps = ec.autograd.eps_chain(Cp, p)
+        eps.backward(G)
+
+    ms = _timed(step, flush_l2, 20, torch)
+    torch.cuda.synchronize()
+    ec.eps_profile_start()
+    for _ in range(10):
+        flush_l2()
+        step()
+    prof = ec.eps_profile_stop()
+    ec.eps_sync_status()
+    peak, _ = measured_peaks()
+    cols = w.nx * w.ny
+    alg = cols * (16 + 12 * w.nz + 16 + (3 * w.slab_nk + 1) * 4 + 16)
+    gbs = alg / (ms * 1e-3) / 1e9
+    assert Cp.grad is not None and bool(torch.isfinite(Cp.grad).all())
+    return {"workload": w.name, "unit": UNIT, "value": w.voxels / (ms * 1e-3),
+            "ms_per_step": round(ms, 4), "step": "eps = EpsChain(C); eps.backward(G)",
+            "kernel_us_avg": {k: round(v[1] / v[0] * 1e3, 2) for k, v in prof.items()},
+            "algorithmic_bytes": alg, "achieved_gbs": round(gbs, 1),
+            "hbm_frac": round(gbs / peak, 4)}
 
 
 def run_tensor_variant(torch, ec, synth, dev, flush_l2):

@@ -18,6 +18,7 @@
 #include "epsc_contract.cuh"
 #include "epsc_contract_tma.cuh"
 #include "epsc_contract_tma_batch.cuh"
+#include "epsc_contract_tma_real.cuh"
 #include "epsc_pack.cuh"
 #include "epsc_launch.h"
 #include "epsc_multi.cuh"
@@ -399,6 +400,46 @@ bool prepare_contract_tma_batch(const std::vector<const Geometry *> &gs,
   return true;
 }
 
+// Column sums of a real cotangent G through bulk tensor copies;
+// EPS_ERR_UNSUPPORTED when G's layout does not suit them (nz not a multiple
+// of 4, G not 16-byte aligned, a support window wider than the box).
+eps_status_t run_contract_tma_real(const Geometry &g, const float *G, float *Wm, int *err,
+                                   cudaStream_t s) {
+  PFN_encodeTiled enc = encode_tiled();
+  if (!enc || (g.nz & 3) || !aligned(G, 16)) return EPS_ERR_UNSUPPORTED;
+  const int lo = g.k0 & ~7;
+  const int hi = (g.k0 + g.nk + 1 + 7) & ~7;
+  if (hi - lo > TMA_REAL_BX_MAX) return EPS_ERR_UNSUPPORTED;
+  ContractTmaRealArgs ta;
+  std::memset(&ta, 0, sizeof(ta));
+  const long ncol = (long)g.nx * g.ny;
+  // (nz floats) x (columns) x (3 components)
+  cuuint64_t dims[3] = {(cuuint64_t)g.nz, (cuuint64_t)ncol, 3};
+  cuuint64_t strides[2] = {(cuuint64_t)g.nz * 4, (cuuint64_t)ncol * g.nz * 4};
+  cuuint32_t box[3] = {(cuuint32_t)(hi - lo), (cuuint32_t)TMA_REAL_BY, 3};
+  cuuint32_t es[3] = {1, 1, 1};
+  if (enc(&ta.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)G, dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return EPS_ERR_UNSUPPORTED;
+  ta.W = Wm;
+  ta.err = err;
+  ta.nx = g.nx;
+  ta.ny = g.ny;
+  ta.k0 = g.k0;
+  ta.nk = g.nk;
+  ta.x0 = lo;
+  ta.bx = hi - lo;
+  int nsm = 0;
+  eps_status_t st = sm_count(&nsm);
+  if (st != EPS_OK) return st;
+  const long nchunks = (ncol + TMA_REAL_BY - 1) / TMA_REAL_BY;
+  const long blocks = std::max<long>(1, std::min<long>(nchunks, (long)nsm * CONTRACT_BLOCKS_PER_SM));
+  const size_t smem = (size_t)TMA_REAL_NSTAGE * 3 * TMA_REAL_BY * ta.bx * 4 + 128;
+  return launch("eps_vjp_real_contract", contract_tma_real_entry(), dim3((unsigned)blocks), smem,
+                &ta, s);
+}
+
 // Packed planes per column (multiple of 4) and bytes of one packed field.
 int packed_planes(const Geometry &g) { return (g.nk + 1 + 3) & ~3; }
 size_t packed_bytes(const Geometry &g) {
@@ -697,7 +738,9 @@ eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float
   ca.err = err;
   ca.G = G;
   ca.W = Wm;
-  if ((st = run_contract(ca, 8, s)) != EPS_OK) return st;
+  st = run_contract_tma_real(r.g, G, Wm, err, s);
+  if (st == EPS_ERR_UNSUPPORTED) st = run_contract(ca, 8, s);
+  if (st != EPS_OK) return st;
   FwdArgs fa;
   fill_fwd_common(fa, r, C, err);
   fa.r.mode = MODE_REAL;

@@ -29,6 +29,8 @@ const void *contract_tma_entry(int n_lambda);
 // Contraction over many regions fed by bulk tensor copies, with room for at
 // least nmaps tensor maps (2 per region and wavelength).
 const void *contract_tma_batch_entry(int nmaps);
+// Column sums of a real cotangent over the support planes, by bulk copies.
+const void *contract_tma_real_entry();
 // One block that waits (bounded) on a barrier nothing arrives at.
 struct SelftestArgs {
   int *err;

@@ -163,6 +163,26 @@ def test_vjp_real_cotangent():
     assert grad_err(g, ref) <= GRAD_TOL
 
 
+@pytest.mark.parametrize("nz,slab_k0,slab_nk", [
+    (16, -1, 11),     # bulk-copy column sums, support window from plane 0
+    (20, 8, 11),      # slab up to the top plane: the box reads past nz (zero fill)
+    (24, 0, 11),      # slab from plane 0
+    (32, -1, 20),     # a 32-float window, the widest the bulk-copy ring takes
+    (48, -1, 40),     # a 48-float window: register loads
+    (72, -1, 66),     # a 72-float window: register loads
+    (22, -1, 11),     # nz not a multiple of 4: register loads
+])
+def test_vjp_real_support_windows(nz, slab_k0, slab_nk):
+    ec = _ec()
+    p, o = problems(66, 98, nz, 4.0, 16.0, slab_k0=slab_k0, slab_nk=slab_nk)
+    rng = np.random.default_rng(nz + slab_nk)
+    C = rng.random((66, 98), dtype=np.float32)
+    G = rng.standard_normal((3, p.nx, p.ny, nz)).astype(np.float32)
+    g = ec.eps_vjp_real(p, to_dev(C), to_dev(G)).cpu().numpy()
+    ec.eps_sync_status()
+    assert grad_err(g, orc.vjp_real(o, C, G)) <= GRAD_TOL
+
+
 def test_vjp_real_odd_nz():
     ec = _ec()
     p, o = problems(40, 72, 15, 3.0, 8.0)
