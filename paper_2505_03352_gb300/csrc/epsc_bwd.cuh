@@ -12,6 +12,7 @@
 #pragma once
 
 #include "epsc_common.cuh"
+#include "epsc_contract_tma.cuh"   // mbarrier and bulk tensor copy helpers
 
 namespace epsc {
 
@@ -24,17 +25,27 @@ struct BwdSmem {
   static constexpr int DA_ALLOC = NSTRIP_MAX * NA_B + 2 * R;   // du rows readable by strips
   static constexpr int DBP = TB + 4 * R;                       // du pitch
   static constexpr int NCI = (TA + 4 * R) / 2 + 3;             // cell rows covering du
-  static constexpr int NCJ = (TB + 4 * R) / 2 + 3;
+  static constexpr int NCJ0 = (TB + 4 * R) / 2 + 3;            // cell columns covering du
+  // Row pitches of the cell maps leave room for a row that starts up to 3
+  // floats after a 16-byte boundary (bulk tensor copies start on one).
+  static constexpr int NCJ = (NCJ0 + 3 + 3) & ~3;
   static constexpr int NC = NCI * NCJ;
-  static constexpr int NGJ = NCJ + 2;                          // Sobel seeds: one-cell halo
+  static constexpr int NGJ = (NCJ0 + 2 + 3 + 3) & ~3;          // Sobel seeds: one-cell halo
   static constexpr int NG = (NCI + 2) * NGJ;
+  // sections start on 128-byte boundaries
   static constexpr int OFF_U = 0;                              // P' deps / 4, then du in place
-  static constexpr int OFF_IE2 = OFF_U + DA_ALLOC * DBP;       // 1 / eps^2
-  static constexpr int OFF_SEED = OFF_IE2 + DA_ALLOC * DBP;    // 6 maps: dA, dH of x, y, z
-  static constexpr int OFF_G = OFF_SEED + 6 * NC;              // 4 maps: dg of U_x, U_y
-  static constexpr int OFF_DU = OFF_G + 4 * NG;                // 2 maps: dU_x, dU_y
-  static constexpr int OFF_DCE = OFF_DU + 2 * NC;
-  static constexpr int TOTAL = OFF_DCE + GA_MAX * GB_MAX;
+  static constexpr int OFF_IE2 = OFF_U + ((DA_ALLOC * DBP + 31) & ~31);     // 1 / eps^2
+  static constexpr int OFF_SEED = OFF_IE2 + ((DA_ALLOC * DBP + 31) & ~31);  // 6 maps: dA, dH of x, y, z
+  static constexpr int OFF_G = OFF_SEED + ((6 * NC + 31) & ~31);            // 4 maps: dg of U_x, U_y
+  static constexpr int OFF_DU = OFF_G + ((4 * NG + 31) & ~31);              // 2 maps: dU_x, dU_y
+  // K^T results: written after the last read of 1 / eps^2, in its place
+  static constexpr int OFF_DCE = OFF_IE2;
+  static_assert(GA_MAX * GB_MAX <= DA_ALLOC * DBP, "K^T results fit in the 1/eps^2 section");
+  static constexpr int TOTAL = OFF_DU + 2 * NC;
+  // rows of the P' / 1/eps^2 box of a tile clear of the region edge
+  static constexpr int DA_BOX = TA + 2 * R;
+  // bytes the four bulk copies of such a tile deliver
+  static constexpr unsigned TMA_BYTES = 4u * (2 * DBP * DA_BOX + 6 * NC + 4 * NG);
   static constexpr size_t BYTES = sizeof(float) * TOTAL;
 };
 
@@ -68,15 +79,17 @@ __device__ __forceinline__ void sobel_t_weights(int t, int n, int bc, float (&wd
   }
 }
 
-// One tile (subpixel rows a0 .., columns b0 ..) of one region `rg`.
-template <int RP1, int BC, class Args>
+// One tile (subpixel rows a0 .., columns b0 ..) of one region `rg`.  With
+// TMA the arguments carry tensor maps of the staged inputs (bwd_tma_kernel:
+// single region, one tile per block, radius class 3 and up).
+template <int RP1, int BC, bool TMA = false, class Args>
 __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, const int a0,
                                          const int b0) {
   using S = BwdSmem<RP1>;
   constexpr int R = S::R;
   constexpr int DBP = S::DBP;
   constexpr bool clamp = BC == EPS_BC_CLAMP;
-  extern __shared__ __align__(16) float smem[];
+  extern __shared__ __align__(128) float smem[];
   float *sU = smem + S::OFF_U;
   float *sIE2 = smem + S::OFF_IE2;
   float *sSeed = smem + S::OFF_SEED;
@@ -109,55 +122,104 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
   griddep_wait();
 
   // ---- stage P' deps / 4, 1/eps^2, the dA/dH seeds and the Sobel seeds ---
-  for (int r = ty; r < DA_USED; r += 8) {
-    const int va = da_lo + r;
-    const bool row_ok = r < DA && (!clamp || (va >= 0 && va < g.mx));
-    const size_t rowo = row_ok ? (size_t)(clamp ? va : wrapi(va, g.mx)) * g.my : 0;
-    for (int c = tx; c < DB; c += 32) {
-      const int vb = db_lo + c;
-      bool ok = row_ok && (!clamp || (vb >= 0 && vb < g.my));
-      size_t o = ok ? rowo + (clamp ? vb : wrapi(vb, g.my)) : 0;
-      if (!EPSC_IN_BOUNDS(o, 1, (size_t)g.mx * g.my, a.err)) ok = false, o = 0;
-      cp_async4(sU + r * DBP + c, rg.pd4 + o, ok);
-      cp_async4(sIE2 + r * DBP + c, rg.ie2 + o, ok);
+  // A tile whose staged windows lie inside the region (no edge fold, no wrap)
+  // takes four bulk tensor copies in the single-region kernel.  Each box
+  // starts at the 16-byte boundary at or below its window's first column;
+  // the views of the staged maps are shifted by the remainder (sh, shj,
+  // shg).  The staged values are those of the element-wise gather below,
+  // which every other tile (and the batched launches) takes.
+  bool staged = false;
+  int sh = 0, shj = 0, shg = 0;
+  if constexpr (TMA) {
+    // (the sections sit on 128-byte boundaries of the dynamic shared memory,
+    // declared 128-byte aligned; a base that were not falls back to the
+    // element-wise gather)
+    if (R >= 2 && (smem_addr(smem) & 127u) == 0u && da_lo >= 0 && da_lo + DA <= g.mx &&
+        db_lo >= 0 && db_lo + DB <= g.my && ci_lo >= 1 && ci_lo + NCI + 1 <= g.nx && cj_lo >= 1 &&
+        cj_lo + NCJ + 1 <= g.ny) {
+      __shared__ uint64_t bar;
+      __shared__ int s_fail;
+      const int xa = db_lo & ~3, xs = cj_lo & ~3, xg = (cj_lo - 1) & ~3;
+      sh = db_lo - xa;
+      shj = cj_lo - xs;
+      shg = cj_lo - 1 - xg;
+      if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        mbar_arrive_expect_tx(&bar, S::TMA_BYTES);
+        tma_load_3d(sU, &a.maps[0], xa, da_lo, 0, &bar);
+        tma_load_3d(sIE2, &a.maps[1], xa, da_lo, 0, &bar);
+        tma_load_3d(sSeed, &a.maps[2], xs, ci_lo, S_DAX, &bar);
+        tma_load_3d(sG, &a.maps[3], xg, ci_lo - 1, S_GXX, &bar);
+        s_fail = 0;
+        if (!mbar_wait_bounded(&bar, 0u)) {
+          // record the timeout; let the copies land before the block leaves
+          atomicOr(a.err, ERRFLAG_TIMEOUT);
+          mbar_wait_bounded(&bar, 0u);
+          s_fail = 1;
+        }
+      }
+      __syncthreads();
+      if (s_fail) return;
+      staged = true;
     }
   }
-  for (int r = ty; r < NCI; r += 8) {
-    const int vi = ci_lo + r;
-    const bool row_ok = !clamp || (vi >= 0 && vi < g.nx);
-    const size_t rowo = row_ok ? (size_t)(clamp ? vi : wrapi(vi, g.nx)) * g.ny : 0;
-    for (int c = tx; c < NCJ; c += 32) {
-      const int vj = cj_lo + c;
-      bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
-      size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
-      if (!EPSC_IN_BOUNDS(o, 1, plane, a.err)) ok = false, o = 0;
-      float *d = sSeed + r * S::NCJ + c;
-      cp_async4(d + 0 * S::NC, rg.seeds + S_DAX * plane + o, ok);
-      cp_async4(d + 1 * S::NC, rg.seeds + S_DHX * plane + o, ok);
-      cp_async4(d + 2 * S::NC, rg.seeds + S_DAY * plane + o, ok);
-      cp_async4(d + 3 * S::NC, rg.seeds + S_DHY * plane + o, ok);
-      cp_async4(d + 4 * S::NC, rg.seeds + S_DAZ * plane + o, ok);
-      cp_async4(d + 5 * S::NC, rg.seeds + S_DHZ * plane + o, ok);
+  if (!staged) {
+    for (int r = ty; r < DA_USED; r += 8) {
+      const int va = da_lo + r;
+      const bool row_ok = r < DA && (!clamp || (va >= 0 && va < g.mx));
+      const size_t rowo = row_ok ? (size_t)(clamp ? va : wrapi(va, g.mx)) * g.my : 0;
+      for (int c = tx; c < DB; c += 32) {
+        const int vb = db_lo + c;
+        bool ok = row_ok && (!clamp || (vb >= 0 && vb < g.my));
+        size_t o = ok ? rowo + (clamp ? vb : wrapi(vb, g.my)) : 0;
+        if (!EPSC_IN_BOUNDS(o, 1, (size_t)g.mx * g.my, a.err)) ok = false, o = 0;
+        cp_async4(sU + r * DBP + c, rg.pd4 + o, ok);
+        cp_async4(sIE2 + r * DBP + c, rg.ie2 + o, ok);
+      }
     }
-  }
-  for (int r = ty; r < NCI + 2; r += 8) {
-    const int vi = ci_lo - 1 + r;
-    const bool row_ok = !clamp || (vi >= 0 && vi < g.nx);
-    const size_t rowo = row_ok ? (size_t)(clamp ? vi : wrapi(vi, g.nx)) * g.ny : 0;
-    for (int c = tx; c < NCJ + 2; c += 32) {
-      const int vj = cj_lo - 1 + c;
-      bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
-      size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
-      if (!EPSC_IN_BOUNDS(o, 1, plane, a.err)) ok = false, o = 0;
-      float *d = sG + r * S::NGJ + c;
-      cp_async4(d + 0 * S::NG, rg.seeds + S_GXX * plane + o, ok);
-      cp_async4(d + 1 * S::NG, rg.seeds + S_GYX * plane + o, ok);
-      cp_async4(d + 2 * S::NG, rg.seeds + S_GXY * plane + o, ok);
-      cp_async4(d + 3 * S::NG, rg.seeds + S_GYY * plane + o, ok);
+    for (int r = ty; r < NCI; r += 8) {
+      const int vi = ci_lo + r;
+      const bool row_ok = !clamp || (vi >= 0 && vi < g.nx);
+      const size_t rowo = row_ok ? (size_t)(clamp ? vi : wrapi(vi, g.nx)) * g.ny : 0;
+      for (int c = tx; c < NCJ; c += 32) {
+        const int vj = cj_lo + c;
+        bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
+        size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
+        if (!EPSC_IN_BOUNDS(o, 1, plane, a.err)) ok = false, o = 0;
+        float *d = sSeed + r * S::NCJ + c;
+        cp_async4(d + 0 * S::NC, rg.seeds + S_DAX * plane + o, ok);
+        cp_async4(d + 1 * S::NC, rg.seeds + S_DHX * plane + o, ok);
+        cp_async4(d + 2 * S::NC, rg.seeds + S_DAY * plane + o, ok);
+        cp_async4(d + 3 * S::NC, rg.seeds + S_DHY * plane + o, ok);
+        cp_async4(d + 4 * S::NC, rg.seeds + S_DAZ * plane + o, ok);
+        cp_async4(d + 5 * S::NC, rg.seeds + S_DHZ * plane + o, ok);
+      }
     }
+    for (int r = ty; r < NCI + 2; r += 8) {
+      const int vi = ci_lo - 1 + r;
+      const bool row_ok = !clamp || (vi >= 0 && vi < g.nx);
+      const size_t rowo = row_ok ? (size_t)(clamp ? vi : wrapi(vi, g.nx)) * g.ny : 0;
+      for (int c = tx; c < NCJ + 2; c += 32) {
+        const int vj = cj_lo - 1 + c;
+        bool ok = row_ok && (!clamp || (vj >= 0 && vj < g.ny));
+        size_t o = ok ? rowo + (clamp ? vj : wrapi(vj, g.ny)) : 0;
+        if (!EPSC_IN_BOUNDS(o, 1, plane, a.err)) ok = false, o = 0;
+        float *d = sG + r * S::NGJ + c;
+        cp_async4(d + 0 * S::NG, rg.seeds + S_GXX * plane + o, ok);
+        cp_async4(d + 1 * S::NG, rg.seeds + S_GYX * plane + o, ok);
+        cp_async4(d + 2 * S::NG, rg.seeds + S_GXY * plane + o, ok);
+        cp_async4(d + 3 * S::NG, rg.seeds + S_GYY * plane + o, ok);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
   }
-  cp_async_wait_all();
-  __syncthreads();
+  // views of the staged maps (shifts are zero on the element-wise path)
+  sU += sh;
+  sIE2 += sh;
+  sSeed += shj;
+  sG += shg;
 
   // ---- Sobel^T: dU_c at the touched cells ----------------------------------
   // interior cells use the plain transposed stencil; cells next to an edge
@@ -265,6 +327,12 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
 template <int RP1, int BC>
 __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ BwdArgsR<RP1> a) {
   bwd_tile<RP1, BC>(a, a.r, blockIdx.y * TA, blockIdx.x * TB);
+}
+
+// The same scatter with bulk-copy staging of the interior tiles.
+template <int RP1, int BC>
+__global__ void __launch_bounds__(NTHREADS) bwd_tma_kernel(const __grid_constant__ BwdTmaArgsR<RP1> a) {
+  bwd_tile<RP1, BC, true>(a, a.r, blockIdx.y * TA, blockIdx.x * TB);
 }
 
 template <int RP1, int BC>

@@ -6,6 +6,7 @@
 // 256-thread blocks.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -60,10 +61,11 @@ __device__ __forceinline__ bool dbg_in_bounds(size_t lo, size_t cnt, size_t n, i
 
 // seed planes, [NSEED][nx][ny]: the stencil writes W-independent factors,
 // the seeds kernel multiplies them by the column's Eq. 1 sums
+// (the six mean seeds first, then the four Sobel seeds: each group is one
+// contiguous block of planes, which the scatter stages as one box)
 enum Seed : int {
-  S_DAX = 0, S_DHX, S_GXX, S_GYX,   // x: dJ/dA_x, dJ/dH_x, dJ/dg_x(U_x), dJ/dg_y(U_x)
-  S_DAY, S_DHY, S_GXY, S_GYY,       // y: same for U_y
-  S_DAZ, S_DHZ,                     // z: dJ/dA_z, dJ/dH_z
+  S_DAX = 0, S_DHX, S_DAY, S_DHY, S_DAZ, S_DHZ,   // dJ/dA_c, dJ/dH_c for c = x, y, z
+  S_GXX, S_GYX, S_GXY, S_GYY,                     // dJ/dg_x, dJ/dg_y of U_x, then of U_y
   NSEED
 };
 
@@ -146,9 +148,25 @@ struct BwdArgsN {
   int *err;
   float w[NW];
 };
+
+// Arguments of the scatter that stages through bulk tensor copies (larger
+// problems; the tensor maps make its parameter block 0.5 KB larger, which
+// would cost the one-wave launch about 1 us).
+template <int NW>
+struct __align__(64) BwdTmaArgsN {
+  BwdRegion r;
+  int *err;
+  // P' deps / 4 and 1 / eps^2 ({my, mx, 1}); the six mean seeds and the four
+  // Sobel seeds ({ny, nx, NSEED}, one box each)
+  CUtensorMap maps[4];
+  float w[NW];
+};
 using BwdArgs = BwdArgsN<MAX_BOX * MAX_BOX>;
 template <int RP1>
 using BwdArgsR = BwdArgsN<(2 * RP1 - 1) * (2 * RP1 - 1)>;
+using BwdTmaArgs = BwdTmaArgsN<MAX_BOX * MAX_BOX>;
+template <int RP1>
+using BwdTmaArgsR = BwdTmaArgsN<(2 * RP1 - 1) * (2 * RP1 - 1)>;
 
 struct BwdBatchArgs {
   int n;

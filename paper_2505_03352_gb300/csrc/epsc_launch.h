@@ -18,6 +18,9 @@ KernelEntry fwd_entry_a(int rp1, int bc, bool batched);
 KernelEntry fwd_entry_b(int rp1, int bc, bool batched);
 KernelEntry bwd_entry_a(int rp1, int bc, bool batched);
 KernelEntry bwd_entry_b(int rp1, int bc, bool batched);
+// Single-region scatter staging interior tiles through bulk tensor copies
+// (radius classes 3 .. 12; {nullptr, 0} otherwise).
+KernelEntry bwd_tma_entry(int rp1, int bc);
 
 // Contraction kernel with 4 or 8 lanes per column.
 const void *contract_entry(int lanes);

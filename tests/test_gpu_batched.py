@@ -237,3 +237,28 @@ def test_register_load_contraction_for_batches_beyond_the_tensor_map_capacity():
         o = orc.Problem(mx=p.mx, my=p.my, nz=p.nz, radius=p.radius, beta=p.beta, bc=p.bc)
         ref = orc.vjp_fields(o, C, [e.cpu().numpy() for e in EF[k]], [e.cpu().numpy() for e in EA[k]])
         assert np.max(np.abs(G[k].cpu().numpy() - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("mx,my,radius,bc", [
+    (1000, 904, 6.0, 0),    # more than one wave of scatter tiles: bulk-copy staging
+    (968, 1000, 3.0, 1),    # periodic: tiles clear of the wrap take the bulk copies
+    (1024, 1000, 11.5, 0),  # the widest halo (radius class 12)
+    (900, 1048, 2.5, 0),    # radius class 3, the smallest with bulk copies
+])
+def test_bulk_copy_staging_equals_elementwise_staging(mx, my, radius, bc):
+    # a single call larger than one wave stages the scatter's inputs of its
+    # interior tiles through bulk tensor copies; a one-region batch stages
+    # every tile element by element: the results agree bit for bit
+    import torch
+
+    import paper_2505_03352_gb300 as ec
+    p = ec.Problem(mx=mx, my=my, nz=16, radius=radius, beta=16.0, bc=bc)
+    C = torch.from_numpy(synth.soi_layout(mx, my, mx + my + 7)).cuda()
+    ef = [torch.from_numpy(synth.complex_field((3, p.nx, p.ny, p.nz), 61))]
+    ea = [torch.from_numpy(synth.complex_field((3, p.nx, p.ny, p.nz), 62))]
+    ef, ea = [x.cuda() for x in ef], [x.cuda() for x in ea]
+    g1, e1 = ec.eps_vjp(p, C, ef, ea, eps_out=True)
+    G, E = ec.BatchedVjp([p], [C], [ef], [ea])()
+    ec.eps_sync_status()
+    assert torch.equal(G[0], g1)
+    assert torch.equal(E[0], e1)
