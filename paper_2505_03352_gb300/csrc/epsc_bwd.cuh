@@ -6,9 +6,12 @@
 // Edge replicate is a many-to-one index map; its transpose folds every
 // contribution that landed outside the region back onto the edge element.
 //
-// Everything the tile needs (u, the seed maps of the touched cells and the
-// Sobel seeds with a one-cell halo) is staged into shared memory with
-// asynchronous copies first, so the global reads are all in flight at once.
+// Everything the tile needs (P'(u) and 1/eps^2 of its subpixels, the seed
+// maps of the touched cells and the Sobel seeds with a one-cell halo) is
+// staged into shared memory first, so the global reads are all in flight at
+// once: by per-element asynchronous copies (bwd_kernel, the batched
+// kernels, and tiles next to the region edge), or, in bwd_tma_kernel (larger
+// problems), by four bulk tensor copies per tile clear of the edge.
 #pragma once
 
 #include "epsc_common.cuh"
