@@ -480,8 +480,10 @@ eps_status_t run_seeds(const SeedsArgs &sa, cudaStream_t s) {
   eps_status_t st = sm_count(&nsm);
   if (st != EPS_OK) return st;
   if (sa.ncol == 0) return EPS_OK;
-  // one thread per column (a full-occupancy elementwise pass), capped for very large calls
-  const long blocks = std::max<long>(1, std::min<long>((sa.ncol + NTHREADS - 1) / NTHREADS, (long)nsm * 64));
+  // one thread per column, or per four columns for one region of whole float4
+  // rows (a full-occupancy elementwise pass), capped for very large calls
+  const long items = (sa.n == 1 && (sa.r[0].ncol & 3) == 0) ? sa.ncol / 4 : sa.ncol;
+  const long blocks = std::max<long>(1, std::min<long>((items + NTHREADS - 1) / NTHREADS, (long)nsm * 64));
   return launch("eps_vjp_seeds", seeds_entry(), dim3((unsigned)blocks), 0, (void *)&sa, s, false);
 }
 

@@ -10,10 +10,38 @@
 
 namespace epsc {
 
+__device__ __forceinline__ float4 mul4(float4 v, float4 w) {
+  return make_float4(v.x * w.x, v.y * w.y, v.z * w.z, v.w * w.w);
+}
+
 __global__ void __launch_bounds__(NTHREADS) seeds_kernel(const __grid_constant__ SeedsArgs a) {
   // the scatter kernel queued behind may begin launching; it waits for this
   // grid before it reads the seeds
   griddep_launch_dependents();
+  if (a.n == 1 && (a.r[0].ncol & 3) == 0) {
+    // one region whose maps are whole float4 rows (the workspace sections are
+    // 256-byte aligned): four columns per thread, 16-byte accesses, the same
+    // products element by element
+    const SeedsRegion &rg = a.r[0];
+    const long p4 = rg.ncol >> 2;
+    const float4 *W = reinterpret_cast<const float4 *>(rg.W);
+    float4 *s = reinterpret_cast<float4 *>(rg.seeds);
+    for (long q = (long)blockIdx.x * NTHREADS + threadIdx.x; q < p4; q += (long)gridDim.x * NTHREADS) {
+      const float4 Wx = __ldg(W + q), Wy = __ldg(W + p4 + q);
+      const float4 Wzi = __ldg(W + 2 * p4 + q), Wzf = __ldg(W + 3 * p4 + q);
+      s[S_DAX * p4 + q] = mul4(s[S_DAX * p4 + q], Wx);
+      s[S_DHX * p4 + q] = mul4(s[S_DHX * p4 + q], Wx);
+      s[S_GXX * p4 + q] = mul4(s[S_GXX * p4 + q], Wx);
+      s[S_GYX * p4 + q] = mul4(s[S_GYX * p4 + q], Wx);
+      s[S_DAY * p4 + q] = mul4(s[S_DAY * p4 + q], Wy);
+      s[S_DHY * p4 + q] = mul4(s[S_DHY * p4 + q], Wy);
+      s[S_GXY * p4 + q] = mul4(s[S_GXY * p4 + q], Wy);
+      s[S_GYY * p4 + q] = mul4(s[S_GYY * p4 + q], Wy);
+      s[S_DAZ * p4 + q] = Wzi;
+      s[S_DHZ * p4 + q] = mul4(s[S_DHZ * p4 + q], Wzf);
+    }
+    return;
+  }
   for (long c = (long)blockIdx.x * NTHREADS + threadIdx.x; c < a.ncol; c += (long)gridDim.x * NTHREADS) {
     int k = 0;
     while (k + 1 < a.n && c >= a.r[k + 1].col_start) ++k;
