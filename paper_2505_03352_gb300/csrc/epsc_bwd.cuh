@@ -82,6 +82,12 @@ __device__ __forceinline__ void sobel_t_weights(int t, int n, int bc, float (&wd
   }
 }
 
+// 16-byte asynchronous copy; both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 // One tile (subpixel rows a0 .., columns b0 ..) of one region `rg`.  With
 // TMA the arguments carry tensor maps of the staged inputs (bwd_tma_kernel:
 // single region, one tile per block, radius class 3 and up).
@@ -167,7 +173,54 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
       staged = true;
     }
   }
-  if (!staged) {
+  // Otherwise a tile whose windows lie inside the region, in maps whose rows
+  // are whole float4 runs, copies 16 bytes at a time from the 16-byte
+  // boundary at or below each window (the same shifted views); the rest
+  // gather element by element.  Every copy stays inside its map.
+  const int xa = db_lo & ~3, xs = cj_lo & ~3, xg = (cj_lo - 1) & ~3;
+  const int nca = (db_lo + DB - xa + 3) >> 2;        // float4 per P' / 1/eps^2 row
+  const int ncs = (cj_lo + NCJ - xs + 3) >> 2;       // per seed row
+  const int ncg = (cj_lo + NCJ + 1 - xg + 3) >> 2;   // per Sobel-seed row
+  const bool vec = !staged && (g.my & 3) == 0 && (g.ny & 3) == 0 && da_lo >= 0 &&
+                   da_lo + DA <= g.mx && DA_USED == DA && db_lo >= 0 && xa + 4 * nca <= g.my &&
+                   ci_lo >= 1 && ci_lo + NCI + 1 <= g.nx && cj_lo >= 1 && xs + 4 * ncs <= g.ny &&
+                   xg + 4 * ncg <= g.ny && 4 * nca <= DBP && 4 * ncs <= S::NCJ && 4 * ncg <= S::NGJ;
+  if (vec) {
+    sh = db_lo - xa;
+    shj = cj_lo - xs;
+    shg = cj_lo - 1 - xg;
+    for (int idx = tid; idx < DA * nca; idx += NTHREADS) {
+      const int r = idx / nca, k = idx - r * nca;
+      const size_t o = (size_t)(da_lo + r) * g.my + xa + 4 * k;
+      if (!EPSC_IN_BOUNDS(o, 4, (size_t)g.mx * g.my, a.err)) continue;
+      cp_async16(sU + r * DBP + 4 * k, rg.pd4 + o);
+      cp_async16(sIE2 + r * DBP + 4 * k, rg.ie2 + o);
+    }
+    for (int idx = tid; idx < NCI * ncs; idx += NTHREADS) {
+      const int r = idx / ncs, k = idx - r * ncs;
+      const size_t o = (size_t)(ci_lo + r) * g.ny + xs + 4 * k;
+      if (!EPSC_IN_BOUNDS(o, 4, plane, a.err)) continue;
+      float *d = sSeed + r * S::NCJ + 4 * k;
+      cp_async16(d + 0 * S::NC, rg.seeds + S_DAX * plane + o);
+      cp_async16(d + 1 * S::NC, rg.seeds + S_DHX * plane + o);
+      cp_async16(d + 2 * S::NC, rg.seeds + S_DAY * plane + o);
+      cp_async16(d + 3 * S::NC, rg.seeds + S_DHY * plane + o);
+      cp_async16(d + 4 * S::NC, rg.seeds + S_DAZ * plane + o);
+      cp_async16(d + 5 * S::NC, rg.seeds + S_DHZ * plane + o);
+    }
+    for (int idx = tid; idx < (NCI + 2) * ncg; idx += NTHREADS) {
+      const int r = idx / ncg, k = idx - r * ncg;
+      const size_t o = (size_t)(ci_lo - 1 + r) * g.ny + xg + 4 * k;
+      if (!EPSC_IN_BOUNDS(o, 4, plane, a.err)) continue;
+      float *d = sG + r * S::NGJ + 4 * k;
+      cp_async16(d + 0 * S::NG, rg.seeds + S_GXX * plane + o);
+      cp_async16(d + 1 * S::NG, rg.seeds + S_GYX * plane + o);
+      cp_async16(d + 2 * S::NG, rg.seeds + S_GXY * plane + o);
+      cp_async16(d + 3 * S::NG, rg.seeds + S_GYY * plane + o);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  } else if (!staged) {
     for (int r = ty; r < DA_USED; r += 8) {
       const int va = da_lo + r;
       const bool row_ok = r < DA && (!clamp || (va >= 0 && va < g.mx));
