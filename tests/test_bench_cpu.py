@@ -1,0 +1,67 @@
+"""Host-side pieces of the benchmark, without a GPU: the algorithmic byte
+counts against the per-column figures of the measurement plan (C read 16 B,
+dJ/dC write 16 B, eps_hat write 12 nz B, 544 B of J-support field planes per
+wavelength), the committed ncu traffic used only for the kernel source it
+was taken on, the roofline peak, and the reference arm's JSON line."""
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+import bench
+from paper_2505_03352_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("cfg,nl,per_column", [(2, 1, 864), (3, 3, 2048), (5, 8, 4768)])
+def test_algorithmic_bytes_per_column(cfg, nl, per_column):
+    w = synth.WORKLOADS[cfg]
+    cols = w.nx * w.ny
+    assert bench.algorithmic_bytes(w, nl) == per_column * cols
+
+
+def test_cfg2_call_and_contraction_bytes():
+    w = synth.WORKLOADS[2]
+    assert bench.algorithmic_bytes(w, 1) == 77_760_000
+    assert bench.contraction_bytes(w, 1) == 50_400_000      # 544 + 16 B per column
+
+
+def test_committed_traffic_needs_the_current_kernel_source(monkeypatch):
+    w = synth.WORKLOADS[2]
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)[w.name]
+    monkeypatch.setattr(bench, "kernel_hash", lambda: rec["kernel_hash"])
+    assert bench.committed_traffic(w.name) == rec["bytes_per_launch"]
+    assert rec["bytes_per_launch"] == rec["dram_read_bytes"] + rec["dram_write_bytes"]
+    monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 16)
+    assert bench.committed_traffic(w.name) is None
+    assert bench.committed_traffic("no such workload") is None
+
+
+def test_measured_peak_is_the_driver_copy_rate():
+    peak, kind = bench.measured_peaks()
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            assert peak == pytest.approx(json.load(f)["hbm_gbs"])
+        assert kind == "measured"
+    else:
+        assert (peak, kind) == (6800.0, "fallback")
+
+
+def test_reference_arm_prints_one_json_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
