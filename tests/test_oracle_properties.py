@@ -1,0 +1,89 @@
+"""Randomised properties of the FP64 oracle over shapes the fixed pins do
+not reach: ragged and non-square regions, radii from below one subpixel to
+5, slabs anywhere in z (including against the top and bottom planes), beta
+up to 32 and both boundary rules.
+
+- Adjoint identity: <vjp_real(G), v> = <G, J v>, with J v the complex-step
+  directional derivative of eps_hat (exact to rounding, no step error).
+- Eq. 1 form: vjp_fields equals -2 Re of vjp_real applied to the summed,
+  unconjugated field product (real and imaginary parts by linearity).
+- Forward bounds: every eps_hat entry lies between eps_clad and eps_core.
+- Filter: under the periodic rule the sum of u equals the sum of C.
+
+The examples are drawn by hypothesis when it is installed."""
+
+import numpy as np
+import pytest
+
+from oracle import epschain_oracle as orc
+
+hyp = pytest.importorskip("hypothesis")
+st = hyp.strategies
+given, settings = hyp.given, hyp.settings
+
+
+@st.composite
+def problems(draw):
+    mx = 2 * draw(st.integers(2, 7))
+    my = 2 * draw(st.integers(2, 7))
+    nz = draw(st.integers(3, 10))
+    nk = draw(st.integers(1, nz - 2))
+    k0 = draw(st.integers(0, nz - 1 - nk))
+    radius = draw(st.sampled_from([0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 4.0, 5.0]))
+    beta = draw(st.sampled_from([1.0, 4.0, 8.0, 16.0, 32.0]))
+    eta = draw(st.sampled_from([0.3, 0.5, 0.7]))
+    bc = draw(st.sampled_from([orc.CLAMP, orc.PERIODIC]))
+    seed = draw(st.integers(0, 2 ** 31 - 1))
+    p = orc.Problem(mx=mx, my=my, nz=nz, radius=radius, beta=beta, eta=eta, bc=bc,
+                    slab_k0=k0, slab_nk=nk)
+    return p, np.random.default_rng(seed)
+
+
+def _jvp(p, C, v, h=1e-30):
+    return np.imag(orc.eps_hat(p, C.astype(np.complex128) + 1j * h * v)) / h
+
+
+@settings(max_examples=40, deadline=None)
+@given(problems())
+def test_vjp_real_is_the_adjoint_of_the_forward_derivative(case):
+    p, rng = case
+    C = rng.random((p.mx, p.my))
+    v = rng.standard_normal((p.mx, p.my))
+    G = rng.standard_normal((3, p.nx, p.ny, p.nz))
+    lhs = float(np.sum(orc.vjp_real(p, C, G) * v))
+    rhs = float(np.sum(G * _jvp(p, C, v)))
+    assert lhs == pytest.approx(rhs, rel=1e-9, abs=1e-12 * (1 + abs(rhs)))
+
+
+@settings(max_examples=25, deadline=None)
+@given(problems(), st.integers(1, 3))
+def test_eq1_form_is_minus_two_re_of_the_real_vjp(case, n_lambda):
+    p, rng = case
+    C = rng.random((p.mx, p.my))
+    shape = (3, p.nx, p.ny, p.nz)
+    EF = [rng.standard_normal(shape) + 1j * rng.standard_normal(shape) for _ in range(n_lambda)]
+    EA = [rng.standard_normal(shape) + 1j * rng.standard_normal(shape) for _ in range(n_lambda)]
+    w = sum(ef * ea for ef, ea in zip(EF, EA))
+    ref = -2.0 * orc.vjp_real(p, C, np.real(w))
+    got = orc.vjp_fields(p, C, EF, EA)
+    np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-10 * (1 + np.abs(ref).max()))
+
+
+@settings(max_examples=40, deadline=None)
+@given(problems())
+def test_eps_hat_lies_between_the_two_materials(case):
+    p, rng = case
+    C = rng.random((p.mx, p.my))
+    e = orc.eps_hat(p, C)
+    assert np.all(e >= p.eps_clad * (1 - 1e-12)) and np.all(e <= p.eps_core * (1 + 1e-12))
+
+
+@settings(max_examples=30, deadline=None)
+@given(problems())
+def test_periodic_filter_preserves_the_sum(case):
+    p, rng = case
+    q = orc.Problem(mx=p.mx, my=p.my, nz=p.nz, radius=p.radius, beta=p.beta, bc=orc.PERIODIC,
+                    slab_k0=p.slab_k0, slab_nk=p.slab_nk)
+    C = rng.random((p.mx, p.my))
+    u = orc.forward(q, C)["u"]
+    assert float(u.sum()) == pytest.approx(float(C.sum()), rel=1e-12)
