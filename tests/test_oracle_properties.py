@@ -9,6 +9,9 @@ up to 32 and both boundary rules.
   unconjugated field product (real and imaginary parts by linearity).
 - Forward bounds: every eps_hat entry lies between eps_clad and eps_core.
 - Filter: under the periodic rule the sum of u equals the sum of C.
+- The same adjoint identity for the morphology chain (random alpha, disk
+  radius and dilate/erode sequences) and for coarse control nodes (random
+  node grids).
 
 The examples are drawn by hypothesis when it is installed."""
 
@@ -87,3 +90,42 @@ def test_periodic_filter_preserves_the_sum(case):
     C = rng.random((p.mx, p.my))
     u = orc.forward(q, C)["u"]
     assert float(u.sum()) == pytest.approx(float(C.sum()), rel=1e-12)
+
+
+@st.composite
+def morphs(draw):
+    from oracle import morph_oracle as mo
+    alpha = draw(st.sampled_from([5.0, 20.0, 60.0]))
+    radius = draw(st.sampled_from([0.0, 0.5, 1.0, 1.5, 2.0, 2.5]))
+    ops = tuple(draw(st.lists(st.sampled_from([mo.DILATE, mo.ERODE]), min_size=0, max_size=4)))
+    return mo.Morph(alpha=alpha, radius=radius, ops=ops)
+
+
+@settings(max_examples=25, deadline=None)
+@given(problems(), morphs())
+def test_morphology_vjp_is_the_adjoint_of_its_forward_derivative(case, morph):
+    from oracle import morph_oracle as mo
+    p, rng = case
+    C = rng.random((p.mx, p.my))
+    v = rng.standard_normal((p.mx, p.my))
+    G = rng.standard_normal((3, p.nx, p.ny, p.nz))
+    h = 1e-30
+    jv = np.imag(mo.eps_hat_morph(p, morph, C.astype(np.complex128) + 1j * h * v)) / h
+    lhs = float(np.sum(mo.vjp_real_morph(p, morph, C, G) * v))
+    rhs = float(np.sum(G * jv))
+    assert lhs == pytest.approx(rhs, rel=1e-8, abs=1e-12 * (1 + abs(rhs)))
+
+
+@settings(max_examples=25, deadline=None)
+@given(problems(), st.integers(2, 6), st.integers(2, 6))
+def test_coarse_vjp_is_the_adjoint_of_its_forward_derivative(case, ncx, ncy):
+    from oracle import coarse_oracle as co
+    p, rng = case
+    c = rng.random((ncx, ncy))
+    v = rng.standard_normal((ncx, ncy))
+    G = rng.standard_normal((3, p.nx, p.ny, p.nz))
+    h = 1e-30
+    jv = np.imag(co.eps_hat_coarse(p, c.astype(np.complex128) + 1j * h * v)) / h
+    lhs = float(np.sum(co.vjp_real_coarse(p, c, G) * v))
+    rhs = float(np.sum(G * jv))
+    assert lhs == pytest.approx(rhs, rel=1e-9, abs=1e-12 * (1 + abs(rhs)))
