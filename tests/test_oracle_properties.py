@@ -12,6 +12,8 @@ up to 32 and both boundary rules.
 - The same adjoint identity for the morphology chain (random alpha, disk
   radius and dilate/erode sequences) and for coarse control nodes (random
   node grids).
+- 3-D face normals: the face rows are those of a unit-normal tensor, and
+  every other plane equals the base chain's.
 
 The examples are drawn by hypothesis when it is installed."""
 
@@ -129,3 +131,32 @@ def test_coarse_vjp_is_the_adjoint_of_its_forward_derivative(case, ncx, ncy):
     lhs = float(np.sum(co.vjp_real_coarse(p, c, G) * v))
     rhs = float(np.sum(G * jv))
     assert lhs == pytest.approx(rhs, rel=1e-9, abs=1e-12 * (1 + abs(rhs)))
+
+
+@settings(max_examples=25, deadline=None)
+@given(problems())
+def test_face_rows_are_those_of_a_unit_normal_tensor(case):
+    # 3-D face normals: on each face plane, row z of T = (a - b) n n^T + b I
+    # with |n| = 1 obeys (T_zz - b)(a - b) = T_zx^2 + T_zy^2 + (T_zz - b)^2,
+    # with T_zz between a and b; other planes equal the base chain's
+    from oracle import normals3d_oracle as n3
+    p, rng = case
+    C = rng.random((p.mx, p.my))
+    eps, od = n3.forward_3d(p, C)
+    fw = orc.forward(p, C, offdiag=True)
+    a = 0.5 * (fw["H"][2] + 1 / p.eps_clad)
+    b = 1 / (0.5 * (fw["A"][2] + p.eps_clad))
+    faces = [p.k0, p.k0 + p.slab_nk]
+    for k in faces:
+        t = 1 / eps[2, :, :, k] - b
+        lhs = t * (a - b)
+        rhs = od[2, :, :, k] ** 2 + od[3, :, :, k] ** 2 + t * t
+        scale = np.abs(a - b).max() ** 2 + 1e-300
+        assert np.max(np.abs(lhs - rhs)) <= 1e-10 * scale
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        te = 1 / eps[2, :, :, k]
+        assert np.all(te >= lo * (1 - 1e-12)) and np.all(te <= hi * (1 + 1e-12))
+    mask = np.ones(p.nz, bool)
+    mask[faces] = False
+    np.testing.assert_array_equal(eps[:2], fw["eps_hat"][:2])
+    np.testing.assert_array_equal(eps[2][..., mask], fw["eps_hat"][2][..., mask])
