@@ -171,11 +171,6 @@ eps_status_t sm_count(int *n) {
   return EPS_OK;
 }
 
-bool profiling() {
-  std::lock_guard<std::mutex> lk(g_prof_mu);
-  return g_prof_on;
-}
-
 // Launch `fn` (one by-value argument struct) on stream s.  With `pdl` the
 // kernel may begin while the previous kernel in the stream is still running
 // (programmatic dependent launch); it must then wait on that grid
@@ -196,8 +191,7 @@ eps_status_t launch(const char *name, const void *fn, dim3 grid, size_t smem, vo
     }
   }
   if (prof && cudaEventRecord(rec.e0, s) != cudaSuccess) return EPS_ERR_CUDA;
-  cudaLaunchConfig_t cfg;
-  std::memset(&cfg, 0, sizeof(cfg));
+  cudaLaunchConfig_t cfg{};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(NTHREADS);
   cfg.dynamicSmemBytes = smem;

@@ -98,13 +98,13 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
   constexpr int R = S::R;
   constexpr int DBP = S::DBP;
   constexpr bool clamp = BC == EPS_BC_CLAMP;
-  extern __shared__ __align__(128) float smem[];
-  float *sU = smem + S::OFF_U;
-  float *sIE2 = smem + S::OFF_IE2;
-  float *sSeed = smem + S::OFF_SEED;
-  float *sG = smem + S::OFF_G;
-  float *sdU = smem + S::OFF_DU;
-  float *sdc = smem + S::OFF_DCE;
+  extern __shared__ __align__(128) float bwd_smem[];
+  float *sU = bwd_smem + S::OFF_U;
+  float *sIE2 = bwd_smem + S::OFF_IE2;
+  float *sSeed = bwd_smem + S::OFF_SEED;
+  float *sG = bwd_smem + S::OFF_G;
+  float *sdU = bwd_smem + S::OFF_DU;
+  float *sdc = bwd_smem + S::OFF_DCE;
 
   const Geometry &g = rg.g;
   const int tid = threadIdx.x;
@@ -143,7 +143,7 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
     // (the sections sit on 128-byte boundaries of the dynamic shared memory,
     // declared 128-byte aligned; a base that were not falls back to the
     // element-wise gather)
-    if (R >= 2 && (smem_addr(smem) & 127u) == 0u && da_lo >= 0 && da_lo + DA <= g.mx &&
+    if (R >= 2 && (smem_addr(bwd_smem) & 127u) == 0u && da_lo >= 0 && da_lo + DA <= g.mx &&
         db_lo >= 0 && db_lo + DB <= g.my && ci_lo >= 1 && ci_lo + NCI + 1 <= g.nx && cj_lo >= 1 &&
         cj_lo + NCJ + 1 <= g.ny) {
       __shared__ uint64_t bar;

@@ -153,7 +153,7 @@ struct BwdArgsN {
 // problems; the tensor maps make its parameter block 0.5 KB larger, which
 // would cost the one-wave launch about 1 us).
 template <int NW>
-struct __align__(64) BwdTmaArgsN {
+struct __align__(128) BwdTmaArgsN {
   BwdRegion r;
   int *err;
   // P' deps / 4 and 1 / eps^2 ({my, mx, 1}); the six mean seeds and the four

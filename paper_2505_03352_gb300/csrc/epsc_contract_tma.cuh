@@ -31,7 +31,7 @@ constexpr int TMA_BX_MAX = 64;    // floats per box row (support window)
 // full-size struct and the launch copies the kernel's parameter bytes, a
 // common prefix (smaller parameter blocks launch faster).
 template <int NMAPS>
-struct __align__(64) ContractTmaArgsN {
+struct __align__(128) ContractTmaArgsN {
   float *W;                                // [4][nx][ny]
   int *err;
   int nx, ny, k0, nk, nlambda;

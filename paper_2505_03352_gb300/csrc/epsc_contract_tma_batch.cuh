@@ -38,7 +38,7 @@ struct ContractTmaBatchRegion {
 // is instantiated for a few map counts and the launch copies only its
 // prefix of the host's full-size struct.
 template <int NMAPS>
-struct __align__(64) ContractTmaBatchArgsN {
+struct __align__(128) ContractTmaBatchArgsN {
   int n, nlambda, nchunks, stage_floats;   // stage_floats: 6 TMA_BY max(bx)
   int *err;
   ContractTmaBatchRegion r[EPS_MAX_BATCH];

@@ -24,7 +24,7 @@ constexpr int TMA_REAL_NSTAGE = 4;
 constexpr int TMA_REAL_BY = 128;      // columns per chunk (box rows)
 constexpr int TMA_REAL_BX_MAX = 32;   // support window per column, floats (ring <= 197 KB)
 
-struct __align__(64) ContractTmaRealArgs {
+struct __align__(128) ContractTmaRealArgs {
   float *W;                 // [4][nx][ny]
   int *err;
   int nx, ny, k0, nk;

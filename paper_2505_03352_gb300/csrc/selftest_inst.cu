@@ -24,7 +24,7 @@ const void *selftest_timeout_entry() { return (const void *)&selftest_timeout_ke
 // EPS_ERR_DEVICE_BOUNDS.  In release builds the check compiles away.
 __global__ void __launch_bounds__(NTHREADS) selftest_bounds_kernel(const __grid_constant__ SelftestArgs a) {
   if (threadIdx.x == 0) {
-    const size_t n = 16;
+    [[maybe_unused]] const size_t n = 16;   // unused where the check compiles away
     if (!EPSC_IN_BOUNDS(n, 1, n, a.err)) return;
   }
 }
