@@ -14,6 +14,10 @@ up to 32 and both boundary rules.
   node grids).
 - 3-D face normals: the face rows are those of a unit-normal tensor, and
   every other plane equals the base chain's.
+- Adam (Eq. 10-11) with a zero stabiliser: scaling every gradient of a
+  multi-step run by a power of two leaves the trajectory bit for bit (the
+  update depends on M / sqrt(V) only), and negating the gradients negates
+  the update from a zero design.
 
 The examples are drawn by hypothesis when it is installed."""
 
@@ -166,3 +170,44 @@ def test_face_rows_are_those_of_a_unit_normal_tensor(case):
     mask[faces] = False
     np.testing.assert_array_equal(eps[:2], fw["eps_hat"][:2])
     np.testing.assert_array_equal(eps[2][..., mask], fw["eps_hat"][2][..., mask])
+
+
+@st.composite
+def adam_runs(draw):
+    steps = draw(st.integers(1, 8))
+    shape = (draw(st.integers(1, 6)), draw(st.integers(1, 6)))
+    b1 = draw(st.sampled_from([0.0, 0.5, 0.9]))
+    b2 = draw(st.sampled_from([0.9, 0.99, 0.999]))
+    k = draw(st.integers(-20, 20))
+    seed = draw(st.integers(0, 2 ** 31 - 1))
+    rng = np.random.default_rng(seed)
+    G = [rng.standard_normal(shape) * 10.0 ** rng.integers(-4, 4, shape) for _ in range(steps)]
+    return b1, b2, k, G, rng.random(shape)
+
+
+def _adam_trajectory(p, C, G):
+    from oracle import optimizer_oracle as oo
+    M = np.zeros_like(C)
+    V = np.zeros_like(C)
+    out = []
+    for i, g in enumerate(G, start=1):
+        C, M, V = oo.adam_update(C, g, M, V, i, p)
+        out.append(C)
+    return out
+
+
+@settings(max_examples=60, deadline=None)
+@given(adam_runs())
+def test_adam_step_is_invariant_to_gradient_scale_and_odd_in_its_sign(run):
+    from oracle import optimizer_oracle as oo
+    b1, b2, k, G, C0 = run
+    p = oo.OptParams(b1=b1, b2=b2, adam_eps=0.0)
+    base = _adam_trajectory(p, C0, G)
+    scaled = _adam_trajectory(p, C0, [np.ldexp(g, k) for g in G])
+    for a, b in zip(base, scaled):
+        np.testing.assert_array_equal(a, b)
+    zero = np.zeros_like(C0)
+    pos = _adam_trajectory(p, zero, G)
+    neg = _adam_trajectory(p, zero, [-g for g in G])
+    for a, b in zip(pos, neg):
+        np.testing.assert_array_equal(a, -b)
