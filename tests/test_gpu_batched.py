@@ -125,6 +125,9 @@ def test_mixed_radius_classes_need_their_own_launch_set():
         assert np.max(np.abs(G[k].cpu().numpy() - g1.cpu().numpy())) <= 1e-5 * g1.abs().max().item()
 
 
+# the last capture is meant to stay empty: tuning refuses to launch while the
+# stream is capturing, and torch warns when such a capture ends
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
 def test_autotuned_shapes_give_identical_results():
     import torch
 
