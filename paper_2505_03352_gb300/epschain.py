@@ -171,25 +171,99 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-def _stream(stream):
+# Device type every tensor argument must have.  The CPU tests of these
+# argument checks set it to "cpu" and replace the library with a recorder;
+# no call ever computes on the host.
+_DEVICE_TYPE = "cuda"
+
+
+def _stream(stream, device=None):
+    """The cudaStream_t handle of `stream` (default: the current stream).
+    With `device`, the stream must belong to it and it must be the current
+    device: the library launches on the current device only."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
+    if device is not None:
+        if stream.device != device:
+            raise ValueError(f"the stream is on {stream.device} but the tensors are on {device}; "
+                             "select their device with torch.cuda.set_device")
+        if device.type == "cuda" and torch.cuda.current_device() != device.index:
+            raise ValueError(f"the tensors are on {device}, which is not the current device; "
+                             "select it with torch.cuda.set_device")
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _need(t, shape, dtype, name):
+def _need(t, shape, dtype, name, device=None):
+    """t is a contiguous tensor of `shape` and `dtype` on the call's device."""
     import torch
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
-    if not t.is_cuda:
+    if t.device.type != _DEVICE_TYPE:
         raise ValueError(f"{name} must be a CUDA tensor")
-    if tuple(t.shape) != tuple(shape):
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device} but the call's tensors are on {device}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
     if t.dtype != dtype:
         raise ValueError(f"{name} has dtype {t.dtype}, expected {dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
+
+
+def _need_bytes(t, nbytes, name, device):
+    """t is a contiguous uint8 buffer of at least `nbytes` bytes on `device`
+    (a workspace, a packed field or the optimiser state)."""
+    import torch
+    _need(t, None, torch.uint8, name, device)
+    if t.numel() < nbytes:
+        raise ValueError(f"{name} holds {t.numel()} bytes, {nbytes} are needed")
+
+
+def _field_ptrs(prob, EF, EA, field_type, device):
+    """Check the per-wavelength field lists and return (n_lambda, EF
+    pointer array, EA pointer array)."""
+    import torch
+    if len(EF) != len(EA):
+        raise ValueError("EF and EA must have the same number of wavelengths")
+    nl = len(EF)
+    if nl > EPS_MAX_LAMBDA:
+        raise ValueError(f"at most {EPS_MAX_LAMBDA} wavelengths per call")
+    if field_type == EPS_FIELD_C64:
+        for l in range(nl):
+            _need(EF[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EF[{l}]", device)
+            _need(EA[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EA[{l}]", device)
+    else:
+        nbytes = eps_packed_field_bytes(prob, field_type)
+        for l in range(nl):
+            _need_bytes(EF[l], nbytes, f"EF[{l}] (packed field)", device)
+            _need_bytes(EA[l], nbytes, f"EA[{l}] (packed field)", device)
+    ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
+    ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
+    return nl, ef, ea
+
+
+def _scales(field_scales, nl):
+    """The per-wavelength field scales as a float array, or None."""
+    if field_scales is None:
+        return None
+    flat = [float(v) for v in _flatten(field_scales)]
+    if len(flat) != 6 * nl:
+        raise ValueError("field_scales must hold n_lambda x 2 x 3 values")
+    return (ctypes.c_float * len(flat))(*flat)
+
+
+def _eps_out(prob, eps_out, device):
+    """(wanted, tensor or None) for an eps_out argument: a tensor, True to
+    allocate one, or None / False for none."""
+    import torch
+    if eps_out is None or eps_out is False:
+        return False, None
+    shape = (3, prob.nx, prob.ny, prob.nz)
+    if eps_out is True:
+        eps_out = torch.empty(shape, dtype=torch.float32, device=device)
+    _need(eps_out, shape, torch.float32, "eps_out", device)
+    return True, eps_out
 
 
 def eps_status_string(status: int) -> str:
@@ -209,17 +283,20 @@ def eps_forward(prob: Problem, C, eps=None, offdiag=None, stream=None):
     prob.flags has EPS_FLAG_OFFDIAG).  Returns eps, or (eps, offdiag)."""
     import torch
     _need(C, (prob.mx, prob.my), torch.float32, "C")
+    dev = C.device
     shape = (3, prob.nx, prob.ny, prob.nz)
     if eps is None:
-        eps = torch.empty(shape, dtype=torch.float32, device=C.device)
-    _need(eps, shape, torch.float32, "eps")
+        eps = torch.empty(shape, dtype=torch.float32, device=dev)
+    _need(eps, shape, torch.float32, "eps", dev)
     want_od = bool(prob.flags & EPS_FLAG_OFFDIAG)
-    if want_od and offdiag is None:
-        n_od = 4 if prob.flags & EPS_FLAG_NORMALS_3D else 2
-        offdiag = torch.empty((n_od,) + shape[1:], dtype=torch.float32, device=C.device)
+    if want_od:
+        od_shape = (4 if prob.flags & EPS_FLAG_NORMALS_3D else 2,) + shape[1:]
+        if offdiag is None:
+            offdiag = torch.empty(od_shape, dtype=torch.float32, device=dev)
+        _need(offdiag, od_shape, torch.float32, "offdiag", dev)
     p = prob.c_struct()
     _check(lib().eps_forward(ctypes.byref(p), _ptr(C), _ptr(eps), _ptr(offdiag) if want_od else None,
-                             _stream(stream)), "eps_forward")
+                             _stream(stream, dev)), "eps_forward")
     return (eps, offdiag) if want_od else eps
 
 
@@ -228,53 +305,31 @@ def _workspace(prob, n_lambda, ws, device):
     need = eps_workspace_size(prob, n_lambda)
     if ws is None:
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
+    _need_bytes(ws, 0, "ws", device)      # its size and alignment are checked by the library
     return ws
 
 
 def eps_vjp(prob: Problem, C, EF, EA, scale: float = -2.0, dJdC=None, eps_out=None,
             field_type: int = EPS_FIELD_C64, field_scales=None, ws=None, stream=None):
     """Eq. 1 adjoint gradient dJ/dC [mx, my] from lists of forward / adjoint
-    field tensors (complex64 [3, nx, ny, nz] for EPS_FIELD_C64).  With
-    eps_out (a tensor, or True to allocate one) the forward eps_hat is
-    written by the same pass.  Returns dJdC, or (dJdC, eps_out)."""
+    field tensors (complex64 [3, nx, ny, nz] for EPS_FIELD_C64, packed uint8
+    buffers from eps_field_pack otherwise).  With eps_out (a tensor, or True
+    to allocate one) the forward eps_hat is written by the same pass.
+    Returns dJdC, or (dJdC, eps_out)."""
     import torch
     _need(C, (prob.mx, prob.my), torch.float32, "C")
-    if len(EF) != len(EA):
-        raise ValueError("EF and EA must have the same number of wavelengths")
-    nl = len(EF)
-    if nl > EPS_MAX_LAMBDA:
-        raise ValueError(f"at most {EPS_MAX_LAMBDA} wavelengths per call")
-    if field_type == EPS_FIELD_C64:
-        for l in range(nl):
-            _need(EF[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EF[{l}]")
-            _need(EA[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EA[{l}]")
-    else:
-        nbytes = eps_packed_field_bytes(prob, field_type)
-        for l in range(nl):
-            for name, t in ((f"EF[{l}]", EF[l]), (f"EA[{l}]", EA[l])):
-                if not (t.is_cuda and t.dtype == torch.uint8 and t.numel() >= nbytes):
-                    raise ValueError(f"{name} must be a packed field buffer of {nbytes} bytes")
+    dev = C.device
+    nl, ef, ea = _field_ptrs(prob, EF, EA, field_type, dev)
+    fs = _scales(field_scales, nl)
     if dJdC is None:
-        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=C.device)
-    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC")
-    ret_eps = eps_out is not None and eps_out is not False
-    if eps_out is True:
-        eps_out = torch.empty((3, prob.nx, prob.ny, prob.nz), dtype=torch.float32, device=C.device)
-    if ret_eps:
-        _need(eps_out, (3, prob.nx, prob.ny, prob.nz), torch.float32, "eps_out")
-    ws = _workspace(prob, nl, ws, C.device)
-    ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
-    ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
-    fs = None
-    if field_scales is not None:
-        flat = [float(v) for v in _flatten(field_scales)]
-        if len(flat) != 6 * nl:
-            raise ValueError("field_scales must hold n_lambda x 2 x 3 values")
-        fs = (ctypes.c_float * len(flat))(*flat)
+        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=dev)
+    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC", dev)
+    ret_eps, eps_out = _eps_out(prob, eps_out, dev)
+    ws = _workspace(prob, nl, ws, dev)
     p = prob.c_struct()
     _check(lib().eps_vjp(ctypes.byref(p), _ptr(C), nl, field_type, ef, ea, fs, float(scale),
-                         _ptr(dJdC), _ptr(eps_out) if ret_eps else None, _ptr(ws), ws.numel(),
-                         _stream(stream)), "eps_vjp")
+                         _ptr(dJdC), _ptr(eps_out), _ptr(ws), ws.numel(), _stream(stream, dev)),
+           "eps_vjp")
     return (dJdC, eps_out) if ret_eps else dJdC
 
 
@@ -293,14 +348,15 @@ def eps_vjp_real(prob: Problem, C, G, dJdC=None, ws=None, stream=None):
     """(d eps_hat / dC)^T G for a real float32 cotangent G [3, nx, ny, nz]."""
     import torch
     _need(C, (prob.mx, prob.my), torch.float32, "C")
-    _need(G, (3, prob.nx, prob.ny, prob.nz), torch.float32, "G")
+    dev = C.device
+    _need(G, (3, prob.nx, prob.ny, prob.nz), torch.float32, "G", dev)
     if dJdC is None:
-        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=C.device)
-    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC")
-    ws = _workspace(prob, 1, ws, C.device)
+        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=dev)
+    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC", dev)
+    ws = _workspace(prob, 1, ws, dev)
     p = prob.c_struct()
     _check(lib().eps_vjp_real(ctypes.byref(p), _ptr(C), _ptr(G), _ptr(dJdC), _ptr(ws), ws.numel(),
-                              _stream(stream)), "eps_vjp_real")
+                              _stream(stream, dev)), "eps_vjp_real")
     return dJdC
 
 
@@ -318,12 +374,14 @@ def eps_field_pack(prob: Problem, field_type: int, E, out=None, stream=None):
     EPS_FIELD_F16X2_SCALED (uint8 device tensor; see include/epschain.h)."""
     import torch
     _need(E, (3, prob.nx, prob.ny, prob.nz), torch.complex64, "E")
+    dev = E.device
     nbytes = eps_packed_field_bytes(prob, field_type)
     if out is None:
-        out = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=E.device)
+        out = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=dev)
+    _need_bytes(out, nbytes, "out", dev)
     p = prob.c_struct()
     _check(lib().eps_field_pack(ctypes.byref(p), field_type, _ptr(E), _ptr(out), out.numel(),
-                                _stream(stream)), "eps_field_pack")
+                                _stream(stream, dev)), "eps_field_pack")
     return out
 
 
@@ -345,17 +403,33 @@ def eps_batched_workspace_size(probs, n_lambda: int = 1) -> int:
     return n.value
 
 
+def _batch_device(probs, Cs):
+    """The device of a batch's controls, after checking that every region
+    has its controls there."""
+    import torch
+    if len(probs) == 0:
+        raise ValueError("a batch needs at least one region")
+    if len(Cs) != len(probs):
+        raise ValueError(f"{len(Cs)} control arrays for {len(probs)} regions")
+    _need(Cs[0], (probs[0].mx, probs[0].my), torch.float32, "C[0]")
+    dev = Cs[0].device
+    for k, p in enumerate(probs):
+        _need(Cs[k], (p.mx, p.my), torch.float32, f"C[{k}]", dev)
+    return dev
+
+
 def eps_forward_batched(probs, Cs, eps=None, stream=None):
     """eps_hat of every region in one call; returns the list of eps tensors."""
     import torch
+    dev = _batch_device(probs, Cs)
     if eps is None:
-        eps = [torch.empty((3, p.nx, p.ny, p.nz), dtype=torch.float32, device=C.device)
-               for p, C in zip(probs, Cs)]
-    for p, C, e in zip(probs, Cs, eps):
-        _need(C, (p.mx, p.my), torch.float32, "C")
-        _need(e, (3, p.nx, p.ny, p.nz), torch.float32, "eps")
+        eps = [torch.empty((3, p.nx, p.ny, p.nz), dtype=torch.float32, device=dev) for p in probs]
+    if len(eps) != len(probs):
+        raise ValueError(f"{len(eps)} eps outputs for {len(probs)} regions")
+    for k, (p, e) in enumerate(zip(probs, eps)):
+        _need(e, (3, p.nx, p.ny, p.nz), torch.float32, f"eps[{k}]", dev)
     _check(lib().eps_forward_batched(len(probs), _probs(probs), _ptrs(Cs), _ptrs(eps),
-                                     _stream(stream)), "eps_forward_batched")
+                                     _stream(stream, dev)), "eps_forward_batched")
     return eps
 
 
@@ -363,23 +437,30 @@ class BatchedVjp:
     """eps_vjp_batched over a fixed set of regions with its arguments built
     once (and its workspace and outputs allocated once), so that the call can
     be repeated or captured in a CUDA graph.  EF[k] / EA[k] are lists of
-    complex64 fields of region k (one per wavelength)."""
+    complex64 fields of region k (one per wavelength, the same number for
+    every region)."""
 
     def __init__(self, probs, Cs, EF, EA, scale=-2.0, with_eps=True, ws=None):
         import torch
+        dev = _batch_device(probs, Cs)
         n = len(probs)
-        nl = len(EF[0]) if n else 0
-        dev = Cs[0].device
+        if len(EF) != n or len(EA) != n:
+            raise ValueError(f"EF and EA must list the fields of each of the {n} regions")
+        nl = len(EF[0])
         for k, p in enumerate(probs):
-            _need(Cs[k], (p.mx, p.my), torch.float32, f"C[{k}]")
+            if len(EF[k]) != nl or len(EA[k]) != nl:
+                raise ValueError(f"region {k} does not have {nl} forward and adjoint fields")
             for l in range(nl):
-                _need(EF[k][l], (3, p.nx, p.ny, p.nz), torch.complex64, f"EF[{k}][{l}]")
-                _need(EA[k][l], (3, p.nx, p.ny, p.nz), torch.complex64, f"EA[{k}][{l}]")
+                _need(EF[k][l], (3, p.nx, p.ny, p.nz), torch.complex64, f"EF[{k}][{l}]", dev)
+                _need(EA[k][l], (3, p.nx, p.ny, p.nz), torch.complex64, f"EA[{k}][{l}]", dev)
+        self._dev = dev
         self.dJdC = [torch.empty((p.mx, p.my), dtype=torch.float32, device=dev) for p in probs]
         self.eps = ([torch.empty((3, p.nx, p.ny, p.nz), dtype=torch.float32, device=dev)
                      for p in probs] if with_eps else None)
         need = eps_batched_workspace_size(probs, nl)
         self.ws = ws if ws is not None else torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        _need_bytes(self.ws, 0, "ws", dev)      # its size and alignment are checked by the library
+        _stream(None, dev)                      # the batch's device is the current one
         self._keep = (Cs, EF, EA)
         self._p = _probs(probs)
         self._C = _ptrs(Cs)
@@ -392,6 +473,8 @@ class BatchedVjp:
         self._fn = lib().eps_vjp_batched
 
     def __call__(self, stream=None):
+        if stream is not None and stream.device != self._dev:
+            raise ValueError(f"the stream is on {stream.device} but the batch is on {self._dev}")
         _check(self._fn(*self._args, _stream(stream)), "eps_vjp_batched")
         return self.dJdC, self.eps
 
@@ -414,8 +497,8 @@ class BatchedVjp:
         caches the fastest for later calls (and graph captures) of this batch
         and returns the choice.  Synchronises; call it before capturing."""
         r = eps_tuning_t()
-        _check(lib().eps_autotune_batched(*self._args, int(reps), ctypes.byref(r), _stream(stream)),
-               "eps_autotune_batched")
+        _check(lib().eps_autotune_batched(*self._args, int(reps), ctypes.byref(r),
+                                          _stream(stream, self._dev)), "eps_autotune_batched")
         return {f: getattr(r, f) for f, _ in eps_tuning_t._fields_}
 
 
@@ -468,28 +551,32 @@ def eps_profile_stop(max_entries: int = 32):
 class PreparedVjp:
     """A fused forward + VJP call (eps_vjp) with its ctypes arguments built
     once, for launch loops where per-call marshalling would dominate.  The
-    tensors passed in are kept alive by this object; calling it launches on
-    `stream` (default: the current stream) and raises on a bad status."""
+    arguments are checked as eps_vjp checks them; the tensors passed in are
+    kept alive by this object; calling it launches on `stream` (default: the
+    current stream) and raises on a bad status."""
 
     def __init__(self, prob: Problem, C, EF, EA, dJdC, eps_out=None, ws=None, scale=-2.0,
                  field_type: int = EPS_FIELD_C64, field_scales=None):
-        nl = len(EF)
+        import torch
+        _need(C, (prob.mx, prob.my), torch.float32, "C")
+        dev = C.device
+        nl, self._ef, self._ea = _field_ptrs(prob, EF, EA, field_type, dev)
+        self._fs = _scales(field_scales, nl)
+        _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC", dev)
+        _, eps_out = _eps_out(prob, eps_out, dev)
+        ws = _workspace(prob, nl, ws, dev)
+        _stream(None, dev)                      # the tensors' device is the current one
+        self._dev = dev
         self._keep = (C, list(EF), list(EA), dJdC, eps_out)
-        if ws is None:
-            ws = _workspace(prob, nl, None, C.device)
         self._ws = ws
         self._p = prob.c_struct()
-        self._ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
-        self._ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
-        self._fs = None
-        if field_scales is not None:
-            flat = [float(v) for v in _flatten(field_scales)]
-            self._fs = (ctypes.c_float * len(flat))(*flat)
         self._args = (ctypes.byref(self._p), _ptr(C), nl, field_type, self._ef, self._ea, self._fs,
                       float(scale), _ptr(dJdC), _ptr(eps_out), _ptr(ws), ws.numel())
         self._fn = lib().eps_vjp
 
     def __call__(self, stream=None):
+        if stream is not None and stream.device != self._dev:
+            raise ValueError(f"the stream is on {stream.device} but the tensors are on {self._dev}")
         _check(self._fn(*self._args, _stream(stream)), "eps_vjp")
 
 
@@ -539,6 +626,7 @@ def _morph_ws(prob, morph, ws, device):
     need = eps_morph_workspace_size(prob, morph)
     if ws is None:
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
+    _need_bytes(ws, 0, "ws", device)      # its size and alignment are checked by the library
     return ws
 
 
@@ -547,18 +635,21 @@ def eps_forward_morph(prob: Problem, morph: Morph, C, eps=None, offdiag=None, ws
     Returns eps, or (eps, offdiag) when prob.flags has EPS_FLAG_OFFDIAG."""
     import torch
     _need(C, (prob.mx, prob.my), torch.float32, "C")
+    dev = C.device
     shape = (3, prob.nx, prob.ny, prob.nz)
     if eps is None:
-        eps = torch.empty(shape, dtype=torch.float32, device=C.device)
-    _need(eps, shape, torch.float32, "eps")
+        eps = torch.empty(shape, dtype=torch.float32, device=dev)
+    _need(eps, shape, torch.float32, "eps", dev)
     want_od = bool(prob.flags & EPS_FLAG_OFFDIAG)
-    if want_od and offdiag is None:
-        offdiag = torch.empty((2,) + shape[1:], dtype=torch.float32, device=C.device)
-    ws = _morph_ws(prob, morph, ws, C.device)
+    if want_od:
+        if offdiag is None:
+            offdiag = torch.empty((2,) + shape[1:], dtype=torch.float32, device=dev)
+        _need(offdiag, (2,) + shape[1:], torch.float32, "offdiag", dev)
+    ws = _morph_ws(prob, morph, ws, dev)
     p, m = prob.c_struct(), morph.c_struct()
     _check(lib().eps_forward_morph(ctypes.byref(p), ctypes.byref(m), _ptr(C), _ptr(eps),
                                    _ptr(offdiag) if want_od else None, _ptr(ws), ws.numel(),
-                                   _stream(stream)), "eps_forward_morph")
+                                   _stream(stream, dev)), "eps_forward_morph")
     return (eps, offdiag) if want_od else eps
 
 
@@ -568,35 +659,18 @@ def eps_vjp_morph(prob: Problem, morph: Morph, C, EF, EA, scale: float = -2.0, d
     dJdC, or (dJdC, eps_out) when eps_out is given (True allocates it)."""
     import torch
     _need(C, (prob.mx, prob.my), torch.float32, "C")
-    if len(EF) != len(EA):
-        raise ValueError("EF and EA must have the same number of wavelengths")
-    nl = len(EF)
-    if nl > EPS_MAX_LAMBDA:
-        raise ValueError(f"at most {EPS_MAX_LAMBDA} wavelengths per call")
-    for l in range(nl):
-        _need(EF[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EF[{l}]")
-        _need(EA[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EA[{l}]")
+    dev = C.device
+    nl, ef, ea = _field_ptrs(prob, EF, EA, EPS_FIELD_C64, dev)
+    fs = _scales(field_scales, nl)
     if dJdC is None:
-        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=C.device)
-    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC")
-    ret_eps = eps_out is not None and eps_out is not False
-    if eps_out is True:
-        eps_out = torch.empty((3, prob.nx, prob.ny, prob.nz), dtype=torch.float32, device=C.device)
-    if ret_eps:
-        _need(eps_out, (3, prob.nx, prob.ny, prob.nz), torch.float32, "eps_out")
-    ws = _morph_ws(prob, morph, ws, C.device)
-    ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
-    ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
-    fs = None
-    if field_scales is not None:
-        flat = [float(v) for v in _flatten(field_scales)]
-        if len(flat) != 6 * nl:
-            raise ValueError("field_scales must hold n_lambda x 2 x 3 values")
-        fs = (ctypes.c_float * len(flat))(*flat)
+        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=dev)
+    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC", dev)
+    ret_eps, eps_out = _eps_out(prob, eps_out, dev)
+    ws = _morph_ws(prob, morph, ws, dev)
     p, m = prob.c_struct(), morph.c_struct()
     _check(lib().eps_vjp_morph(ctypes.byref(p), ctypes.byref(m), _ptr(C), nl, EPS_FIELD_C64, ef, ea,
-                               fs, float(scale), _ptr(dJdC), _ptr(eps_out) if ret_eps else None,
-                               _ptr(ws), ws.numel(), _stream(stream)), "eps_vjp_morph")
+                               fs, float(scale), _ptr(dJdC), _ptr(eps_out), _ptr(ws), ws.numel(),
+                               _stream(stream, dev)), "eps_vjp_morph")
     return (dJdC, eps_out) if ret_eps else dJdC
 
 
@@ -604,36 +678,45 @@ def eps_vjp_real_morph(prob: Problem, morph: Morph, C, G, dJdC=None, ws=None, st
     """(d eps_hat / dC)^T G through the chain with morphology."""
     import torch
     _need(C, (prob.mx, prob.my), torch.float32, "C")
-    _need(G, (3, prob.nx, prob.ny, prob.nz), torch.float32, "G")
+    dev = C.device
+    _need(G, (3, prob.nx, prob.ny, prob.nz), torch.float32, "G", dev)
     if dJdC is None:
-        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=C.device)
-    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC")
-    ws = _morph_ws(prob, morph, ws, C.device)
+        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=dev)
+    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC", dev)
+    ws = _morph_ws(prob, morph, ws, dev)
     p, m = prob.c_struct(), morph.c_struct()
     _check(lib().eps_vjp_real_morph(ctypes.byref(p), ctypes.byref(m), _ptr(C), _ptr(G), _ptr(dJdC),
-                                    _ptr(ws), ws.numel(), _stream(stream)), "eps_vjp_real_morph")
+                                    _ptr(ws), ws.numel(), _stream(stream, dev)),
+           "eps_vjp_real_morph")
     return dJdC
 
 
 class PreparedVjpMorph:
-    """eps_vjp_morph with its ctypes arguments built once (complex64 fields)."""
+    """eps_vjp_morph with its ctypes arguments built once (complex64 fields),
+    checked as eps_vjp_morph checks them."""
 
     def __init__(self, prob: Problem, morph: Morph, C, EF, EA, dJdC, eps_out=None, ws=None,
                  scale=-2.0):
-        nl = len(EF)
+        import torch
+        _need(C, (prob.mx, prob.my), torch.float32, "C")
+        dev = C.device
+        nl, self._ef, self._ea = _field_ptrs(prob, EF, EA, EPS_FIELD_C64, dev)
+        _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC", dev)
+        _, eps_out = _eps_out(prob, eps_out, dev)
+        ws = _morph_ws(prob, morph, ws, dev)
+        _stream(None, dev)                      # the tensors' device is the current one
+        self._dev = dev
         self._keep = (C, list(EF), list(EA), dJdC, eps_out)
-        if ws is None:
-            ws = _morph_ws(prob, morph, None, C.device)
         self._ws = ws
         self._p, self._m = prob.c_struct(), morph.c_struct()
-        self._ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
-        self._ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
         self._args = (ctypes.byref(self._p), ctypes.byref(self._m), _ptr(C), nl, EPS_FIELD_C64,
                       self._ef, self._ea, None, float(scale), _ptr(dJdC), _ptr(eps_out), _ptr(ws),
                       ws.numel())
         self._fn = lib().eps_vjp_morph
 
     def __call__(self, stream=None):
+        if stream is not None and stream.device != self._dev:
+            raise ValueError(f"the stream is on {stream.device} but the tensors are on {self._dev}")
         _check(self._fn(*self._args, _stream(stream)), "eps_vjp_morph")
 
 
@@ -673,13 +756,18 @@ class OptParams:
         return o
 
 
+OPT_STATE_BYTES = 32
+
+
 def eps_opt_init(opt: OptParams, state=None, device=None, stream=None):
     """Device optimiser state (a 32-byte uint8 tensor) set to iteration 0."""
     import torch
     if state is None:
-        state = torch.zeros(32, dtype=torch.uint8, device=device or "cuda")
+        state = torch.zeros(OPT_STATE_BYTES, dtype=torch.uint8, device=device or "cuda")
+    _need(state, (OPT_STATE_BYTES,), torch.uint8, "state")
     o = opt.c_struct()
-    _check(lib().eps_opt_init(ctypes.byref(o), _ptr(state), _stream(stream)), "eps_opt_init")
+    _check(lib().eps_opt_init(ctypes.byref(o), _ptr(state), _stream(stream, state.device)),
+           "eps_opt_init")
     return state
 
 
@@ -696,13 +784,17 @@ def eps_opt_step(prob: Problem, opt: OptParams, state, C, G, M, V, ws, morph=Non
     the VJP call (base chain, or morphology when `morph` is given) that
     evaluated C at beta = prob.beta."""
     import torch
-    for name, t in (("C", C), ("G", G), ("M", M), ("V", V)):
-        _need(t, (prob.mx, prob.my), torch.float32, name)
+    _need(C, (prob.mx, prob.my), torch.float32, "C")
+    dev = C.device
+    for name, t in (("G", G), ("M", M), ("V", V)):
+        _need(t, (prob.mx, prob.my), torch.float32, name, dev)
+    _need(state, (OPT_STATE_BYTES,), torch.uint8, "state", dev)
+    _need_bytes(ws, 0, "ws", dev)      # its size and alignment are checked by the library
     p, o = prob.c_struct(), opt.c_struct()
     m = morph.c_struct() if morph is not None else None
     _check(lib().eps_opt_step(ctypes.byref(p), ctypes.byref(m) if m is not None else None,
                               ctypes.byref(o), _ptr(state), _ptr(C), _ptr(G), _ptr(M), _ptr(V),
-                              _ptr(ws), ws.numel(), _stream(stream)), "eps_opt_step")
+                              _ptr(ws), ws.numel(), _stream(stream, dev)), "eps_opt_step")
 
 
 # ------------------------------------------------------ coarse control grid
@@ -738,6 +830,7 @@ def _coarse_ws(prob, coarse, ws, device):
     if ws is None:
         ws = torch.empty(max(eps_coarse_workspace_size(prob, coarse), 1), dtype=torch.uint8,
                          device=device)
+    _need_bytes(ws, 0, "ws", device)      # its size and alignment are checked by the library
     return ws
 
 
@@ -745,16 +838,18 @@ def eps_forward_coarse(prob: Problem, coarse: Coarse, c, eps=None, ws=None, stre
     """eps_hat [3, nx, ny, nz] from node values c [ncx, ncy]."""
     import torch
     _need(c, (coarse.ncx, coarse.ncy), torch.float32, "c")
+    dev = c.device
     shape = (3, prob.nx, prob.ny, prob.nz)
     if eps is None:
-        eps = torch.empty(shape, dtype=torch.float32, device=c.device)
-    _need(eps, shape, torch.float32, "eps")
+        eps = torch.empty(shape, dtype=torch.float32, device=dev)
+    _need(eps, shape, torch.float32, "eps", dev)
     if prob.flags & EPS_FLAG_OFFDIAG:
         raise ValueError("use the C entry point for the off-diagonal term with coarse controls")
-    ws = _coarse_ws(prob, coarse, ws, c.device)
+    ws = _coarse_ws(prob, coarse, ws, dev)
     p, g = prob.c_struct(), coarse.c_struct()
     _check(lib().eps_forward_coarse(ctypes.byref(p), ctypes.byref(g), _ptr(c), _ptr(eps), None,
-                                    _ptr(ws), ws.numel(), _stream(stream)), "eps_forward_coarse")
+                                    _ptr(ws), ws.numel(), _stream(stream, dev)),
+           "eps_forward_coarse")
     return eps
 
 
@@ -764,39 +859,33 @@ def eps_vjp_coarse(prob: Problem, coarse: Coarse, c, EF, EA, scale: float = -2.0
     dJdc [ncx, ncy], or (dJdc, eps_out) when eps_out is given (True allocates)."""
     import torch
     _need(c, (coarse.ncx, coarse.ncy), torch.float32, "c")
-    nl = len(EF)
-    if len(EA) != nl or nl > EPS_MAX_LAMBDA:
-        raise ValueError("EF and EA must list the same number (<= 16) of wavelengths")
-    for l in range(nl):
-        _need(EF[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EF[{l}]")
-        _need(EA[l], (3, prob.nx, prob.ny, prob.nz), torch.complex64, f"EA[{l}]")
+    dev = c.device
+    nl, ef, ea = _field_ptrs(prob, EF, EA, EPS_FIELD_C64, dev)
     if dJdc is None:
-        dJdc = torch.empty((coarse.ncx, coarse.ncy), dtype=torch.float32, device=c.device)
-    _need(dJdc, (coarse.ncx, coarse.ncy), torch.float32, "dJdc")
-    ret_eps = eps_out is not None and eps_out is not False
-    if eps_out is True:
-        eps_out = torch.empty((3, prob.nx, prob.ny, prob.nz), dtype=torch.float32, device=c.device)
-    if ret_eps:
-        _need(eps_out, (3, prob.nx, prob.ny, prob.nz), torch.float32, "eps_out")
-    ws = _coarse_ws(prob, coarse, ws, c.device)
-    ef = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EF])
-    ea = (ctypes.c_void_p * max(nl, 1))(*[t.data_ptr() for t in EA])
+        dJdc = torch.empty((coarse.ncx, coarse.ncy), dtype=torch.float32, device=dev)
+    _need(dJdc, (coarse.ncx, coarse.ncy), torch.float32, "dJdc", dev)
+    ret_eps, eps_out = _eps_out(prob, eps_out, dev)
+    ws = _coarse_ws(prob, coarse, ws, dev)
     p, g = prob.c_struct(), coarse.c_struct()
     _check(lib().eps_vjp_coarse(ctypes.byref(p), ctypes.byref(g), _ptr(c), nl, EPS_FIELD_C64, ef, ea,
-                                None, float(scale), _ptr(dJdc), _ptr(eps_out) if ret_eps else None,
-                                _ptr(ws), ws.numel(), _stream(stream)), "eps_vjp_coarse")
+                                None, float(scale), _ptr(dJdc), _ptr(eps_out), _ptr(ws), ws.numel(),
+                                _stream(stream, dev)), "eps_vjp_coarse")
     return (dJdc, eps_out) if ret_eps else dJdc
 
 
 def eps_vjp_real_coarse(prob: Problem, coarse: Coarse, c, G, dJdc=None, ws=None, stream=None):
+    """(d eps_hat / dc)^T G with respect to the node values, for a real
+    float32 cotangent G [3, nx, ny, nz]."""
     import torch
     _need(c, (coarse.ncx, coarse.ncy), torch.float32, "c")
-    _need(G, (3, prob.nx, prob.ny, prob.nz), torch.float32, "G")
+    dev = c.device
+    _need(G, (3, prob.nx, prob.ny, prob.nz), torch.float32, "G", dev)
     if dJdc is None:
-        dJdc = torch.empty((coarse.ncx, coarse.ncy), dtype=torch.float32, device=c.device)
-    _need(dJdc, (coarse.ncx, coarse.ncy), torch.float32, "dJdc")
-    ws = _coarse_ws(prob, coarse, ws, c.device)
+        dJdc = torch.empty((coarse.ncx, coarse.ncy), dtype=torch.float32, device=dev)
+    _need(dJdc, (coarse.ncx, coarse.ncy), torch.float32, "dJdc", dev)
+    ws = _coarse_ws(prob, coarse, ws, dev)
     p, g = prob.c_struct(), coarse.c_struct()
     _check(lib().eps_vjp_real_coarse(ctypes.byref(p), ctypes.byref(g), _ptr(c), _ptr(G), _ptr(dJdc),
-                                     _ptr(ws), ws.numel(), _stream(stream)), "eps_vjp_real_coarse")
+                                     _ptr(ws), ws.numel(), _stream(stream, dev)),
+           "eps_vjp_real_coarse")
     return dJdc
