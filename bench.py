@@ -227,7 +227,6 @@ def contraction_bytes(w, n_lambda):
 
 def cpu_baseline(w, budget_s: float = 15.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload."""
-    import numpy as np
     from oracle import epschain_oracle as orc
     from paper_2505_03352_gb300 import synth
     C = synth.controls(w)
@@ -251,7 +250,6 @@ def cpu_baseline(w, budget_s: float = 15.0):
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args, rank, world, local):
-    import numpy as np
     import torch
 
     import paper_2505_03352_gb300 as ec
@@ -498,28 +496,6 @@ def _device_fields(torch, shape, n, seed, dev):
     return out
 
 
-def _window_error(w, C, EF, EA, g_gpu, half=48):
-    """max |dJ/dC - oracle| / max |oracle| on windows of the full problem."""
-    import numpy as np
-    from oracle import epschain_oracle as orc
-    margin = int(2 * np.ceil(w.radius)) + 8
-    worst = 0.0
-    for (ca, cb) in [(0, 0), (w.mx // 2, w.my // 2), (w.mx, w.my)]:
-        a0 = max(0, ca - half) // 2 * 2
-        b0 = max(0, cb - half) // 2 * 2
-        a1, b1 = min(w.mx, a0 + 2 * half), min(w.my, b0 + 2 * half)
-        wa0, wb0 = max(0, a0 - margin), max(0, b0 - margin)
-        wa1, wb1 = min(w.mx, a1 + margin), min(w.my, b1 + margin)
-        o = orc.Problem(mx=wa1 - wa0, my=wb1 - wb0, nz=w.nz, radius=w.radius, beta=w.beta)
-        sl = (slice(None), slice(wa0 // 2, wa1 // 2), slice(wb0 // 2, wb1 // 2), slice(None))
-        ref = orc.vjp_fields(o, C[wa0:wa1, wb0:wb1], [e[sl].cpu().numpy() for e in EF],
-                             [e[sl].cpu().numpy() for e in EA])
-        rg = ref[a0 - wa0:a1 - wa0, b0 - wb0:b1 - wb0]
-        gg = g_gpu[a0:a1, b0:b1]
-        worst = max(worst, float(np.max(np.abs(gg - rg)) / np.max(np.abs(rg))))
-    return worst
-
-
 def run_variants(torch, ec, synth, dev, flush_l2,
                  sel=("cfg3", "cfg4", "cfg5", "morph", "opt", "coarse", "normals3d", "autograd")):
     """The differentiation (cfg3), batching (cfg4) and precision (cfg5) forms,
@@ -607,22 +583,22 @@ def run_variants(torch, ec, synth, dev, flush_l2,
         res = {}
         call = ec.PreparedVjp(p, C, EF, EA, G, eps_out=E)
         ms = _timed(call, flush_l2, 10, torch)
-        err = _window_error(w, Ch, EF, EA, G.cpu().numpy())
         res["fp32"] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
-                       "algorithmic_bytes": algorithmic_bytes(w, 8),
-                       "dJdC_max_err_vs_fp64_oracle": err}
+                       "algorithmic_bytes": algorithmic_bytes(w, 8)}
         for name, ft in (("bf16", ec.EPS_FIELD_BF16X2_SCALED), ("fp16", ec.EPS_FIELD_F16X2_SCALED)):
             PF = [ec.eps_field_pack(p, ft, e) for e in EF]
             PA = [ec.eps_field_pack(p, ft, e) for e in EA]
             call = ec.PreparedVjp(p, C, PF, PA, G, eps_out=E, field_type=ft)
             ms = _timed(call, flush_l2, 10, torch)
-            err = _window_error(w, Ch, EF, EA, G.cpu().numpy())
             alg = 8 * w.mx * w.my + 12 * w.nx * w.ny * w.nz + w.nx * w.ny * 8 * (3 * w.slab_nk + 1) * 2 * 4
             res[name] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
-                         "algorithmic_bytes": alg, "dJdC_max_err_vs_fp64_oracle": err,
+                         "algorithmic_bytes": alg,
                          "packed_bytes_per_field": ec.eps_packed_field_bytes(p, ft)}
             del PF, PA, call
-        out["cfg5_precision_8wavelengths"] = dict(workload=w.name, unit=UNIT, **res)
+        out["cfg5_precision_8wavelengths"] = dict(
+            workload=w.name, unit=UNIT,
+            parity=("tests/test_gpu_large.py: dJ/dC against the FP64 oracle within 1e-4 (FP32), "
+                    "2e-2 (BF16) and 2e-3 (FP16) of its largest value"), **res)
         del C, EF, EA, G, E
     if "morph" in sel:
         out["cfg2_morphology"] = run_morph_variant(torch, ec, synth, dev, flush_l2)
@@ -644,7 +620,6 @@ def run_autograd_variant(torch, ec, synth, dev, flush_l2):
     density and projection from C.  Algorithmic bytes per Yee column: C read
     twice (16 B each), eps_hat written (12 nz), G read on its 3 nk + 1
     support planes (4 B each) and dJ/dC written (16 B)."""
-    import numpy as np
     w = synth.WORKLOADS[3]
     p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
     Cp = torch.from_numpy(synth.controls(w)).to(dev).requires_grad_(True)
@@ -717,11 +692,8 @@ def run_morph_variant(torch, ec, synth, dev, flush_l2):
     alpha = 20 (App. B), disks of diameter 40 nm and 150 nm (radius 2 and
     7.5 subpixels at 10 nm).  The fused call is timed like the main
     workload; each map kernel is timed with the library's per-kernel events
-    in a separate loop; the r = 2 result is checked against the FP64
-    oracle on the full problem."""
-    import numpy as np
-    from oracle import epschain_oracle as orc
-    from oracle import morph_oracle as mo
+    in a separate loop.  Its parity with the FP64 oracle on the full cfg2
+    problem is the business of tests/test_gpu_morph.py."""
     w = synth.WORKLOADS[2]
     p = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
     Ch = synth.controls(w)
@@ -747,29 +719,18 @@ def run_morph_variant(torch, ec, synth, dev, flush_l2):
         prof = ec.eps_profile_stop()
         ec.eps_sync_status()
         kern = {k: round(v[1] / v[0] * 1e3, 2) for k, v in prof.items()}
-        entry = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
-                 "kernel_us_avg": kern}
-        if mr == 2.0:
-            om = mo.Morph(alpha=20.0, radius=mr)
-            o = orc.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
-            ref = mo.vjp_fields_morph(o, om, Ch, EFh, EAh)
-            ref_e = mo.eps_hat_morph(o, om, Ch)
-            g, e = G.cpu().numpy(), E.cpu().numpy()
-            entry["dJdC_max_err_vs_fp64_oracle"] = float(np.max(np.abs(g - ref)) / np.max(np.abs(ref)))
-            entry["eps_max_rel_err_vs_fp64_oracle"] = float(np.max(np.abs(e - ref_e) / ref_e))
-        res[f"disk_radius_{mr:g}"] = entry
+        res[f"disk_radius_{mr:g}"] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
+                                      "kernel_us_avg": kern}
     return res
 
 
 def run_coarse_variant(torch, ec, synth, dev, flush_l2):
     """The paper's coarse parametrisation: a 210 x 210-cell design region
     (420 x 420 subpixels, nz = 24, cfg2 slab) driven by 36 x 36 control nodes
-    (Eq. 2, hat basis), fused forward + VJP with one wavelength, checked
-    against the FP64 oracle."""
+    (Eq. 2, hat basis), fused forward + VJP with one wavelength.  Its parity
+    with the FP64 oracle is the business of tests/test_gpu_coarse.py."""
     import ctypes
     import numpy as np
-    from oracle import coarse_oracle as co
-    from oracle import epschain_oracle as orc
     mx = my = 420
     nz, ncx, ncy = 24, 36, 36
     p = ec.Problem(mx=mx, my=my, nz=nz, radius=1.0, beta=16.0)
@@ -802,14 +763,10 @@ def run_coarse_variant(torch, ec, synth, dev, flush_l2):
         call()
     prof = ec.eps_profile_stop()
     ec.eps_sync_status()
-    o = orc.Problem(mx=mx, my=my, nz=nz, radius=1.0, beta=16.0)
-    ref = co.vjp_fields_coarse(o, ch, EFh, EAh)
-    err = float(np.max(np.abs(dc.cpu().numpy() - ref)) / np.max(np.abs(ref)))
     vox = (mx // 2) * (my // 2) * nz
     return {"workload": "210x210x24 cells, 36x36 control nodes, beta 16, 1 wavelength",
             "value": vox / (ms * 1e-3), "unit": UNIT, "ms_per_call": round(ms, 4),
-            "kernel_us_avg": {k: round(v[1] / v[0] * 1e3, 2) for k, v in prof.items()},
-            "dJdc_max_err_vs_fp64_oracle": err}
+            "kernel_us_avg": {k: round(v[1] / v[0] * 1e3, 2) for k, v in prof.items()}}
 
 
 def run_opt_variant(torch, ec, synth, dev, flush_l2):
@@ -867,7 +824,6 @@ def run_reference(args, rank, world):
     w = synth.WORKLOADS[2]
     C = synth.controls(w)
     EF, EA = synth.fields(w)
-    op = orc.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
 
     def step(win):
         sl = (slice(0, win), slice(0, win))
