@@ -8,7 +8,8 @@ the chain is kept alive between forward and backward.
 
 For the optimiser loop of the paper, where the cotangent is the Eq. 1 field
 product, adjoint_gradient() makes one fused call that returns eps_hat and
-dJ/dC together.
+dJ/dC together, and EpsAdjoint exposes the same call to autograd as a
+scalar whose gradient is Eq. 1.
 """
 
 from __future__ import annotations
@@ -49,6 +50,41 @@ def adjoint_gradient(prob: Problem, C, EF, EA, scale: float = -2.0, field_type: 
     dJdC, eps = eps_vjp(prob, C, EF, EA, scale=scale, eps_out=True, field_type=field_type,
                         field_scales=field_scales, ws=ws, stream=stream)
     return eps, dJdC
+
+
+class EpsAdjoint(torch.autograd.Function):
+    """Scalar surrogate of the adjoint method (Eq. 1):
+
+        S(C) = sum over the Yee grid of eps_hat(C) * w,
+        w = scale Re(sum_l E_F,l * E_A,l)   (unconjugated, held fixed),
+
+    so that dS/dC = J^T w is Eq. 1's dJ/dC (scale = -2).  The forward makes
+    one fused eps_vjp call, which writes eps_hat and dJ/dC in the same pass,
+    and saves dJ/dC; the backward scales it by the incoming gradient.  The
+    value of S is a torch reduction over eps_hat and the field product,
+    for autograd's bookkeeping only.  The fields are complex64 lists (one
+    tensor per wavelength) and are not differentiated."""
+
+    @staticmethod
+    def forward(ctx, C, prob: Problem, EF, EA, scale: float = -2.0):
+        C = C.contiguous()
+        dJdC, eps = eps_vjp(prob, C, EF, EA, scale=scale, eps_out=True)
+        S = torch.zeros((), dtype=eps.dtype, device=eps.device)
+        for ef, ea in zip(EF, EA):
+            S = S + torch.sum(eps * (ef.real * ea.real - ef.imag * ea.imag))
+        ctx.save_for_backward(dJdC)
+        return scale * S
+
+    @staticmethod
+    def backward(ctx, grad_S):
+        (dJdC,) = ctx.saved_tensors
+        return grad_S * dJdC, None, None, None, None
+
+
+def eps_adjoint(C, prob: Problem, EF, EA, scale: float = -2.0):
+    """The Eq. 1 surrogate S(C) (see EpsAdjoint); S.backward() leaves
+    dJ/dC in C.grad."""
+    return EpsAdjoint.apply(C, prob, list(EF), list(EA), scale)
 
 
 class EpsChainMorph(torch.autograd.Function):
