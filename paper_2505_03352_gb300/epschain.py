@@ -419,8 +419,13 @@ def _batch_device(probs, Cs):
 
 
 def eps_forward_batched(probs, Cs, eps=None, stream=None):
-    """eps_hat of every region in one call; returns the list of eps tensors."""
+    """eps_hat of every region in one call; returns the list of eps tensors
+    (an empty batch is a no-op, as in the C call)."""
     import torch
+    if len(probs) == 0 and len(Cs) == 0 and not eps:
+        _check(lib().eps_forward_batched(0, _probs(probs), _ptrs([]), _ptrs([]), _stream(stream)),
+               "eps_forward_batched")
+        return []
     dev = _batch_device(probs, Cs)
     if eps is None:
         eps = [torch.empty((3, p.nx, p.ny, p.nz), dtype=torch.float32, device=dev) for p in probs]

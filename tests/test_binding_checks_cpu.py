@@ -94,6 +94,8 @@ def test_valid_calls_reach_the_library_with_the_callers_pointers(rec):
     probs = [P, eb.Problem(mx=8, my=10, nz=10, radius=1.0, beta=4.0, slab_nk=4)]
     Cs = [_C(), torch.rand((8, 10))]
     eb.eps_forward_batched(probs, Cs)
+    assert eb.eps_forward_batched([], []) == []              # empty batch: a no-op call
+    assert rec[-1][0] == "eps_forward_batched" and rec[-1][1][0] == 0
     EFb = [EF, [torch.zeros((3, 4, 5, 10), dtype=torch.complex64)] * 2]
     bv = eb.BatchedVjp(probs, Cs, EFb, EFb)
     bv()
@@ -114,7 +116,8 @@ def test_valid_calls_reach_the_library_with_the_callers_pointers(rec):
     eb.eps_vjp_real_coarse(P, cg, c, torch.zeros(SHAPE))
     assert launches(rec) == [
         "eps_forward", "eps_vjp", "eps_vjp", "eps_vjp_real", "eps_forward", "eps_field_pack",
-        "eps_vjp", "eps_forward_batched", "eps_vjp_batched", "eps_vjp_batched", "eps_vjp",
+        "eps_vjp", "eps_forward_batched", "eps_forward_batched", "eps_vjp_batched",
+        "eps_vjp_batched", "eps_vjp",
         "eps_forward_morph", "eps_vjp_morph", "eps_vjp_real_morph", "eps_vjp_morph",
         "eps_opt_init", "eps_opt_step", "eps_forward_coarse", "eps_vjp_coarse",
         "eps_vjp_real_coarse"]
@@ -151,7 +154,8 @@ def _bad_cases():
             field_type=eb.EPS_FIELD_BF16X2_SCALED),
         "pack out float32": lambda: eb.eps_field_pack(P, eb.EPS_FIELD_BF16X2_SCALED, EF[0],
                                                       out=torch.empty(64)),
-        "empty batch": lambda: eb.eps_forward_batched([], []),
+        "empty prepared batch": lambda: eb.BatchedVjp([], [], [], []),
+        "batch controls without regions": lambda: eb.eps_forward_batched([], [C]),
         "batch controls short": lambda: eb.eps_forward_batched(probs, [C]),
         "batch eps short": lambda: eb.eps_forward_batched(probs, [C, C], eps=[torch.empty(SHAPE)]),
         "batch fields short": lambda: eb.BatchedVjp(probs, [C, C], [EF], [EA]),
