@@ -241,7 +241,6 @@ def cpu_baseline(w, budget_s: float = 15.0):
         if time.perf_counter() - t0 > budget_s or reps >= 20:
             break
     dt = time.perf_counter() - t0
-    del np
     return {"value": reps * w.voxels / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{reps} full forward+VJP calls of {w.name} (numpy float64, single thread)",
             "seconds": round(dt, 2)}
@@ -461,7 +460,6 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-    del np
 
 
 # ------------------------------------------------------------------ variants

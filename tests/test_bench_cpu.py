@@ -65,3 +65,11 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_cpu_baseline_times_the_oracle_on_a_bounded_sample():
+    w = synth.WORKLOADS[1]
+    cpu = bench.cpu_baseline(w, budget_s=0.5)
+    assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["unit"] == bench.UNIT
+    assert cpu["value"] > 0 and 0 < cpu["seconds"] < 60
+    assert w.name in cpu["sample"]
