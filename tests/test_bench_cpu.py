@@ -73,3 +73,27 @@ def test_cpu_baseline_times_the_oracle_on_a_bounded_sample():
     assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["unit"] == bench.UNIT
     assert cpu["value"] > 0 and 0 < cpu["seconds"] < 60
     assert w.name in cpu["sample"]
+
+
+def test_gpu_arm_runs_end_to_end_on_a_stand_in_device():
+    # bench.py's GPU arm, every variant included, driven on the CPU with
+    # torch.cuda and the library stubbed (tests/_bench_stand_in.py): its host
+    # logic must produce the one JSON line with every key of the contract
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "_bench_stand_in.py")],
+                       cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "roofline",
+              "cpu_baseline", "e2e", "gpu_launches", "clocks"):
+        assert k in d, k
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["n_gpus"] == 1
+    assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(d["roofline"])
+    assert {"value", "unit", "cores", "kind", "sample"} <= set(d["cpu_baseline"])
+    assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
+    assert d["gpu_launches"] > 0
+    assert set(d["variants"]) >= {"cfg3_fp32_3wavelengths", "cfg4_batched_64_regions",
+                                  "cfg5_precision_8wavelengths", "cfg2_morphology", "optimizer_step",
+                                  "coarse_controls", "forward_tensor_cfg2", "autograd_cfg3"}
