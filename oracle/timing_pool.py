@@ -1,0 +1,85 @@
+"""Process pool that times the FP64 oracle on every host core at once, for the
+CPU-baseline leg of the benchmark.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test-suite, the smoke check
+and the CPU-baseline leg of the benchmark may import this module.  It runs
+the oracle as it stands: each worker draws the seeded inputs of the workload
+itself, computes eps_hat and the Eq. 1 VJP of the whole problem `reps`
+times, and reports its own elapsed time.  The workers start from a shared
+barrier, so the timed parts overlap.  The pool uses the spawn start method,
+which is safe after CUDA has been initialised in the parent.
+"""
+
+from __future__ import annotations
+
+import multiprocessing as mp
+import os
+import time
+
+_barrier = None
+
+
+def _init(barrier):
+    global _barrier
+    _barrier = barrier
+
+
+def _worker(task):
+    cfg, reps = task
+    from paper_2505_03352_gb300 import synth
+
+    from . import epschain_oracle as orc
+    try:
+        w = synth.WORKLOADS[cfg]
+        C = synth.controls(w)
+        EF, EA = synth.fields(w)
+        p = orc.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+    except BaseException:
+        _barrier.abort()          # the other workers stop waiting at once
+        raise
+    _barrier.wait(timeout=120)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        orc.eps_hat(p, C)
+        orc.vjp_fields(p, C, EF, EA)
+    return reps * w.voxels, time.perf_counter() - t0
+
+
+def _mem_available_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def default_workers(per_worker_bytes: int = 4 << 30, ceiling: int = 32) -> int:
+    """One worker per core this process may run on, at most `ceiling`, and
+    no more than the available memory holds at `per_worker_bytes` each (a
+    whole cfg2 call of the oracle peaks near 1 GB)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        cores = os.cpu_count() or 1
+    n = min(cores, ceiling)
+    mem = _mem_available_bytes()
+    if mem is not None:
+        n = min(n, mem // per_worker_bytes)
+    return max(1, int(n))
+
+
+def all_cores(cfg: int, reps: int = 2, workers: int | None = None):
+    """(voxels per second over all workers, workers, seconds): every worker
+    runs `reps` whole forward + VJP calls of workload `cfg`; the rate is the
+    voxels of all workers over the slowest worker's time."""
+    n = workers or default_workers()
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(n)
+    with ctx.Pool(n, initializer=_init, initargs=(barrier,)) as pool:
+        res = pool.map(_worker, [(cfg, reps)] * n, chunksize=1)
+    vox = sum(v for v, _ in res)
+    slowest = max(t for _, t in res)
+    return vox / slowest, n, slowest

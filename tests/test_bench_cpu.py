@@ -73,6 +73,11 @@ def test_cpu_baseline_times_the_oracle_on_a_bounded_sample():
     assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["unit"] == bench.UNIT
     assert cpu["value"] > 0 and 0 < cpu["seconds"] < 60
     assert w.name in cpu["sample"]
+    allc = cpu["all_cores"]
+    from oracle import timing_pool
+    assert allc["cores"] == timing_pool.default_workers() and allc["value"] > 0, allc
+    assert 1 <= timing_pool.default_workers() <= 32
+    assert timing_pool.default_workers(per_worker_bytes=1 << 50) == 1     # memory caps the pool
 
 
 def test_gpu_arm_runs_end_to_end_on_a_stand_in_device():
