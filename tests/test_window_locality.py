@@ -1,6 +1,7 @@
 """The locality that the full-size GPU checks rest on, pinned on the CPU.
 
-tests/test_gpu_large.py checks the cfg3 / cfg5 / cfg4 results on windows:
+tests/test_gpu_large.py checks the cfg3 / cfg5 / cfg4 results on windows
+(window_check, and window_check_device for fields held as tensors):
 the oracle runs on a window grown by a margin of 2 ceil(R) + 8 subpixels
 (cut at the region edge, where the same clamp rule applies) and is compared
 with the full-size result in the window's interior.  Here the full-size
@@ -14,7 +15,7 @@ import pytest
 
 from oracle import epschain_oracle as orc
 from paper_2505_03352_gb300 import synth
-from tests.test_gpu_large import window_check
+from tests.test_gpu_large import window_check, window_check_device
 
 
 def _problem(radius, seed):
@@ -34,6 +35,12 @@ def test_window_recompute_is_exact_in_the_interior(radius):
     g = orc.vjp_fields(o, C, EF, EA)
     windows = [(0, 0), (w.mx // 2, w.my // 2), (w.mx, w.my), (0, w.my), (77, 131)]
     worst_e, worst_g = window_check(w, C, EF, EA, e, g, windows, half=24)
+    assert worst_e <= 1e-13, worst_e
+    assert worst_g <= 1e-12, worst_g
+    # the form the cfg5 check uses, slicing field tensors in place
+    import torch
+    worst_e, worst_g = window_check_device(w, C, [torch.from_numpy(x) for x in EF],
+                                           [torch.from_numpy(x) for x in EA], e, g, windows, half=24)
     assert worst_e <= 1e-13, worst_e
     assert worst_g <= 1e-12, worst_g
 
