@@ -363,9 +363,16 @@ def run_ours(args, rank, world, local):
     alg_c = contraction_bytes(w, 1)
     achieved = alg_c / (c_ms * 1e-3) / 1e9
     call_alg = algorithmic_bytes(w, 1)
+    traffic = committed_traffic(w.name)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": committed_traffic(w.name),
+                "traffic": traffic,
+                # DRAM bytes actually moved (whole 32-byte sectors of the field
+                # columns) per second against the peak, and the algorithmic
+                # fraction the field layout allows at most
+                "dram_frac": (round(traffic / (c_ms * 1e-3) / 1e9 / peak, 4)
+                              if traffic and c_ms > 0 else None),
+                "layout_ceiling_frac": round(alg_c / traffic, 4) if traffic else None,
                 "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if peak_kind == "measured"
                                 else "fallback 6.8 TB/s (of fallback)"),
                 "algorithmic_bytes_per_launch": alg_c, "avg_launch_ms": round(c_ms, 5),

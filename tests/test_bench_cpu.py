@@ -96,6 +96,11 @@ def test_gpu_arm_runs_end_to_end_on_a_stand_in_device():
         assert k in d, k
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["n_gpus"] == 1
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(d["roofline"])
+    rf = d["roofline"]
+    if rf["traffic"]:                       # the committed capture matches the kernel source
+        assert rf["layout_ceiling_frac"] == round(bench.contraction_bytes(synth.WORKLOADS[2], 1)
+                                                  / rf["traffic"], 4)
+        assert rf["dram_frac"] > 0
     assert {"value", "unit", "cores", "kind", "sample"} <= set(d["cpu_baseline"])
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] > 0
