@@ -26,8 +26,8 @@ the repository):
     of Eq. 4 with an unnormalised disk would shift a uniform density by
     log(area)/alpha);
   * the default sequence is a closing followed by an opening: dilate, erode,
-    erode, dilate (the paper names "dilate and erode" and "erode and
-    dilate" combinations);
+    erode, dilate (the paper names both orders in which the two operations
+    can be combined);
   * Phi of Eq. 3 is the filtered density minus the threshold, u - eta, as in
     the base chain;
   * the morphology uses the same boundary rule as the filter (edge replicate

@@ -35,8 +35,8 @@ at the Ey points (the base chain's two maps), then eta_zx and eta_zy at the
 Ez points (non-zero on the two face planes only).  eta_xz at Ex and eta_yz
 at Ey vanish identically in this geometry (n_z = 0 there).  Readings: the
 half-filled cell's in-plane density, the Sobel-consistent z difference and
-the fallback are this module's reading of "normal vector to the interface"
-(Sec. 3) for cells the paper's 2-D Sobel does not cover.
+the fallback are this module's reading of the interface normal (Sec. 3)
+for cells the paper's 2-D Sobel does not cover.
 """
 
 from __future__ import annotations

@@ -19,16 +19,16 @@ design and the gradient G of iteration i both taken at beta_i):
 
 Readings where the paper is silent (each also listed in the design notes of
 the repository):
-  * a subpixel is "gray" when its projected density is strictly between
+  * a subpixel counts as gray when its projected density is strictly between
     gray_tol and 1 - gray_tol (default 0.05), i.e. rho (1 - rho) >
     gray_tol (1 - gray_tol);
   * u is floored at one subpixel (1 / (mx my)), so 1/u stays finite;
   * t has no stated initial value: it starts at its first sample
     (1/u_1 - 1) / beta_1, after which the moving average applies;
     beta_max starts at a given beta_max0;
-  * adam_eps (the paper's "small number") defaults to 1e-8, and the Adam
-    learning rate is `lr` (the paper's eta, renamed to keep eta for the
-    projection threshold); App. B: b1 = 0.9, b2 = 0.999, lr = 0.001,
+  * adam_eps (the small constant the paper adds to the denominator)
+    defaults to 1e-8, and the Adam learning rate is `lr` (the paper's eta,
+    renamed to keep eta for the projection threshold); App. B: b1 = 0.9, b2 = 0.999, lr = 0.001,
     gamma = 0.95, u_0 = 0.01, beta_min = 10;
   * the schedule's i is the 1-based iteration index of Adam's bias
     correction, so beta_N = beta_max at the last iteration.
