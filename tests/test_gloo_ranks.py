@@ -52,3 +52,24 @@ def test_single_process_value():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.weak_scaling_value(10, 1, 4, 2.0) == pytest.approx(10 * 4 / 2e-3)
+
+
+def test_launcher_environment_is_read(monkeypatch):
+    import bench
+    monkeypatch.setenv("RANK", "3")
+    monkeypatch.setenv("WORLD_SIZE", "4")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    assert bench.dist_env() == (3, 4, 1)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k)
+    assert bench.dist_env() == (0, 1, 0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys):
+    # under torchrun the other ranks return at once, without work or output
+    import argparse
+
+    import bench
+    args = argparse.Namespace(steps=1, warmup=1)
+    assert bench.run_reference(args, rank=1, world=2) is None
+    assert capsys.readouterr().out == ""
