@@ -602,6 +602,14 @@ def run_variants(torch, ec, synth, dev, flush_l2,
         ms = _timed(call, flush_l2, 10, torch)
         res["fp32"] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
                        "algorithmic_bytes": algorithmic_bytes(w, 8)}
+        torch.cuda.synchronize()
+        G32 = G.clone()
+        g32_max = float(G32.abs().max())
+
+        def deviation_from_fp32():
+            # max |dJ/dC - dJ/dC of the FP32 path| / max |dJ/dC of the FP32 path|
+            torch.cuda.synchronize()
+            return float((G - G32).abs().max()) / g32_max if g32_max > 0 else None
         for name, ft in (("bf16", ec.EPS_FIELD_BF16X2_SCALED), ("fp16", ec.EPS_FIELD_F16X2_SCALED)):
             PF = [ec.eps_field_pack(p, ft, e) for e in EF]
             PA = [ec.eps_field_pack(p, ft, e) for e in EA]
@@ -610,8 +618,10 @@ def run_variants(torch, ec, synth, dev, flush_l2,
             alg = 8 * w.mx * w.my + 12 * w.nx * w.ny * w.nz + w.nx * w.ny * 8 * (3 * w.slab_nk + 1) * 2 * 4
             res[name] = {"value": w.voxels / (ms * 1e-3), "ms_per_call": round(ms, 4),
                          "algorithmic_bytes": alg,
+                         "dJdC_max_dev_vs_fp32_path": deviation_from_fp32(),
                          "packed_bytes_per_field": ec.eps_packed_field_bytes(p, ft)}
             del PF, PA, call
+        del G32
         out["cfg5_precision_8wavelengths"] = dict(
             workload=w.name, unit=UNIT,
             parity=("tests/test_gpu_large.py: dJ/dC against the FP64 oracle within 1e-4 (FP32), "

@@ -104,6 +104,8 @@ def test_gpu_arm_runs_end_to_end_on_a_stand_in_device():
     assert {"value", "unit", "cores", "kind", "sample"} <= set(d["cpu_baseline"])
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] > 0
+    c5 = d["variants"]["cfg5_precision_8wavelengths"]
+    assert "dJdC_max_dev_vs_fp32_path" in c5["bf16"] and "dJdC_max_dev_vs_fp32_path" in c5["fp16"]
     assert set(d["variants"]) >= {"cfg3_fp32_3wavelengths", "cfg4_batched_64_regions",
                                   "cfg5_precision_8wavelengths", "cfg2_morphology", "optimizer_step",
                                   "coarse_controls", "forward_tensor_cfg2", "autograd_cfg3"}
