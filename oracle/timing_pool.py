@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import multiprocessing as mp
 import os
+import sys
 import time
 
 _barrier = None
@@ -24,9 +25,22 @@ def _init(barrier):
     _barrier = barrier
 
 
+def _synth():
+    """The seeded-input module, loaded from its file: importing it through
+    its package would import torch in every worker."""
+    import importlib.util
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2505_03352_gb300", "synth.py")
+    spec = importlib.util.spec_from_file_location("_timing_pool_synth", path)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[spec.name] = mod          # dataclasses resolve the module by name
+    spec.loader.exec_module(mod)
+    return mod
+
+
 def _worker(task):
     cfg, reps = task
-    from paper_2505_03352_gb300 import synth
+    synth = _synth()
 
     from . import epschain_oracle as orc
     try:
