@@ -155,6 +155,29 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
                      void *ws, size_t ws_bytes, eps_stream_t stream);
 
 /*
+ * eps_vjp plus the value of the Eq. 1 surrogate whose gradient dJdC is:
+ *   S = sum over the J-support voxels of eps_hat * W,
+ * W as for eps_vjp (scale * Re(sum_l s_l E_F,l (.) E_A,l)).  The J-support
+ * voxels are those whose eps_hat depends on C: Ex and Ey planes k0+1 ..
+ * k0+nk and Ez planes k0 .. k0+nk (Sec. 3 extrusion with the z rules of
+ * eps_forward); the other voxels hold eps_clad and would add a constant
+ * independent of C.  This is the adjoint method's linearisation of the
+ * objective around the current design (Eq. 1: dS/dC = dJ/dC) and gives
+ * automatic-differentiation frameworks a scalar to hang the gradient on.
+ *   S   device double, 8-byte aligned, overwritten (set to 0 on the stream
+ *       first, then accumulated by the kernels in FP64; the order of the
+ *       additions is not fixed, so S can differ between calls in its last
+ *       bits)
+ * Other arguments, results and errors as eps_vjp; a NULL or misaligned S
+ * returns EPS_ERR_INVALID_ARG.  An empty problem or n_lambda = 0 gives S = 0.
+ */
+eps_status_t eps_vjp_surrogate(const eps_problem_t *prob, const float *C, int32_t n_lambda,
+                               int32_t field_type, const void *const *EF, const void *const *EA,
+                               const float *field_scales, float scale, float *dJdC,
+                               float *eps_out, double *S, void *ws, size_t ws_bytes,
+                               eps_stream_t stream);
+
+/*
  * Vector-Jacobian product for an arbitrary real cotangent (Sec. 3, end):
  *   dJdC = (d eps_hat / dC)^T G,   G device float32 [3][nx][ny][nz].
  * Used by autograd backward passes; recomputes the forward from C.
@@ -451,10 +474,14 @@ eps_status_t eps_selftest_bounds(eps_stream_t stream);
  *   - Arguments are those of eps_vjp minus ws / ws_bytes; results are the
  *     same as eps_vjp's.
  *   - Problems whose eps_workspace_size() exceeds EPS_STATIC_WS_BYTES are
- *     rejected with EPS_ERR_WORKSPACE before any launch (about 190 000 Yee
- *     columns, e.g. 436 x 436).
+ *     rejected with EPS_ERR_WORKSPACE before any launch (104 bytes per Yee
+ *     column: about 161 000 columns, e.g. 400 x 400).
  *   - The first call on a device looks up the array's device address (set-up,
- *     once per device); make that first call before any stream capture.
+ *     once per device, with that device current); make that first call
+ *     before any stream capture.  The address is kept for the rest of the
+ *     process and belongs to the device's primary context: calls made with
+ *     another context current on that device, or after cudaDeviceReset()
+ *     on it, are not supported.
  *   - All calls on a device share the one array: calls that can overlap on
  *     the GPU (different streams, or host threads without ordering) race and
  *     must be serialised by the caller.  Nothing in the array needs to start

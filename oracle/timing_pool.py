@@ -4,8 +4,9 @@ CPU-baseline leg of the benchmark.
 TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test-suite, the smoke check
 and the CPU-baseline leg of the benchmark may import this module.  It runs
 the oracle as it stands: each worker draws the seeded inputs of the workload
-itself, computes eps_hat and the Eq. 1 VJP of the whole problem `reps`
-times, and reports its own elapsed time.  The workers start from a shared
+itself (the whole problem, or a square window of it for workloads too large
+for one host process), computes eps_hat and the Eq. 1 VJP `reps` times, and
+reports its own elapsed time.  The workers start from a shared
 barrier, so the timed parts overlap.  The pool uses the spawn start method,
 which is safe after CUDA has been initialised in the parent.
 """
@@ -39,14 +40,29 @@ def _synth():
 
 
 def _worker(task):
-    cfg, reps = task
+    cfg, reps, window, index = task
     synth = _synth()
 
     from . import epschain_oracle as orc
     try:
         w = synth.WORKLOADS[cfg]
-        C = synth.controls(w)
-        EF, EA = synth.fields(w)
+        if window:
+            # a window of the given size (an int for a square) with the
+            # workload's layout statistics, depth and wavelength count
+            # (seeds offset per worker)
+            import dataclasses
+            wa, wb = (window, window) if isinstance(window, int) else tuple(window)
+            w = dataclasses.replace(w, mx=wa, my=wb)
+            C = synth.soi_layout(wa, wb, 1000 * (1000 + w.cfg) + index) \
+                if w.layout == "soi" else synth.uniform_controls(wa, wb, 1000 + index)
+            shape = synth.field_shape(w)
+            EF = [synth.complex_field(shape, 1000 * (2000 + 10 * w.cfg + l) + index)
+                  for l in range(w.n_lambda)]
+            EA = [synth.complex_field(shape, 1000 * (3000 + 10 * w.cfg + l) + index)
+                  for l in range(w.n_lambda)]
+        else:
+            C = synth.controls(w)
+            EF, EA = synth.fields(w)
         p = orc.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
     except BaseException:
         _barrier.abort()          # the other workers stop waiting at once
@@ -85,15 +101,17 @@ def default_workers(per_worker_bytes: int = 4 << 30, ceiling: int = 32) -> int:
     return max(1, int(n))
 
 
-def all_cores(cfg: int, reps: int = 2, workers: int | None = None):
+def all_cores(cfg: int, reps: int = 2, workers: int | None = None, window=0):
     """(voxels per second over all workers, workers, seconds): every worker
-    runs `reps` whole forward + VJP calls of workload `cfg`; the rate is the
-    voxels of all workers over the slowest worker's time."""
+    runs `reps` forward + VJP calls of workload `cfg` (the whole problem, or
+    a window of it when `window` is non-zero: an int for a square window of
+    that many controls per side, or (mx, my)); the rate is the voxels of all
+    workers over the slowest worker's time."""
     n = workers or default_workers()
     ctx = mp.get_context("spawn")
     barrier = ctx.Barrier(n)
     with ctx.Pool(n, initializer=_init, initargs=(barrier,)) as pool:
-        res = pool.map(_worker, [(cfg, reps)] * n, chunksize=1)
+        res = pool.map(_worker, [(cfg, reps, window, i) for i in range(n)], chunksize=1)
     vox = sum(v for v, _ in res)
     slowest = max(t for _, t in res)
     return vox / slowest, n, slowest

@@ -13,7 +13,7 @@ from .epschain import (BatchedVjp, eps_batched_workspace_size, eps_forward_batch
                        eps_profile_start, eps_profile_stop, eps_set_l2_fetch_granularity,
                        eps_selftest_timeout, eps_selftest_bounds,
                        eps_status_string, eps_sync_status,
-                       eps_vjp, eps_vjp_real, eps_workspace_size, lib,
+                       eps_vjp, eps_vjp_real, eps_vjp_surrogate, eps_workspace_size, lib,
                        CLOSE_THEN_OPEN, EPS_MORPH_DILATE, EPS_MORPH_ERODE, Morph,
                        eps_forward_morph, eps_morph_workspace_size, eps_vjp_morph,
                        eps_vjp_real_morph, PreparedVjpMorph,
@@ -29,7 +29,7 @@ __all__ = [
     "eps_profile_start", "eps_profile_stop", "eps_set_l2_fetch_granularity",
     "eps_selftest_timeout", "eps_selftest_bounds", "eps_status_string",
     "eps_sync_status", "eps_vjp",
-    "eps_vjp_real", "eps_workspace_size", "lib",
+    "eps_vjp_real", "eps_vjp_surrogate", "eps_workspace_size", "lib",
     "CLOSE_THEN_OPEN", "EPS_MORPH_DILATE", "EPS_MORPH_ERODE", "Morph", "eps_forward_morph",
     "eps_morph_workspace_size", "eps_vjp_morph", "eps_vjp_real_morph", "PreparedVjpMorph",
     "OptParams", "eps_opt_init", "eps_opt_step", "read_opt_state",

@@ -8,8 +8,8 @@ the chain is kept alive between forward and backward.
 
 For the optimiser loop of the paper, where the cotangent is the Eq. 1 field
 product, adjoint_gradient() makes one fused call that returns eps_hat and
-dJ/dC together, and EpsAdjoint exposes the same call to autograd as a
-scalar whose gradient is Eq. 1.
+dJ/dC together, and EpsAdjoint exposes the fused call to autograd as a
+scalar (computed by the library) whose gradient is Eq. 1.
 """
 
 from __future__ import annotations
@@ -17,7 +17,7 @@ from __future__ import annotations
 import torch
 
 from .epschain import (EPS_FIELD_C64, Morph, Problem, eps_forward, eps_forward_morph, eps_vjp,
-                       eps_vjp_real, eps_vjp_real_morph)
+                       eps_vjp_real, eps_vjp_real_morph, eps_vjp_surrogate)
 
 
 class EpsChain(torch.autograd.Function):
@@ -55,36 +55,40 @@ def adjoint_gradient(prob: Problem, C, EF, EA, scale: float = -2.0, field_type: 
 class EpsAdjoint(torch.autograd.Function):
     """Scalar surrogate of the adjoint method (Eq. 1):
 
-        S(C) = sum over the Yee grid of eps_hat(C) * w,
+        S(C) = sum over the J-support voxels of eps_hat(C) * w,
         w = scale Re(sum_l E_F,l * E_A,l)   (unconjugated, held fixed),
 
-    so that dS/dC = J^T w is Eq. 1's dJ/dC (scale = -2).  The forward makes
-    one fused eps_vjp call, which writes eps_hat and dJ/dC in the same pass,
-    and saves dJ/dC; the backward scales it by the incoming gradient.  The
-    value of S is a torch reduction over eps_hat and the field product,
-    for autograd's bookkeeping only.  The fields are complex64 lists (one
-    tensor per wavelength) and are not differentiated."""
+    so that dS/dC = J^T w is Eq. 1's dJ/dC (scale = -2).  The J-support
+    voxels are those where eps_hat depends on C; the cladding voxels would
+    only add a constant.  The forward makes one eps_vjp_surrogate call,
+    which computes dJ/dC, S (FP64, summed on the device) and, if asked,
+    eps_hat in the same pass; it saves dJ/dC, and the backward scales it by
+    the incoming gradient.  The fields are complex64 lists (one tensor per
+    wavelength) and are not differentiated; eps_hat, when returned, is not
+    differentiable either."""
 
     @staticmethod
-    def forward(ctx, C, prob: Problem, EF, EA, scale: float = -2.0):
+    def forward(ctx, C, prob: Problem, EF, EA, scale: float = -2.0, with_eps: bool = False):
         C = C.contiguous()
-        dJdC, eps = eps_vjp(prob, C, EF, EA, scale=scale, eps_out=True)
-        S = torch.zeros((), dtype=eps.dtype, device=eps.device)
-        for ef, ea in zip(EF, EA):
-            S = S + torch.sum(eps * (ef.real * ea.real - ef.imag * ea.imag))
+        if with_eps:
+            dJdC, eps, S = eps_vjp_surrogate(prob, C, EF, EA, scale=scale, eps_out=True)
+            ctx.mark_non_differentiable(eps)
+        else:
+            dJdC, S = eps_vjp_surrogate(prob, C, EF, EA, scale=scale)
         ctx.save_for_backward(dJdC)
-        return scale * S
+        return (S, eps) if with_eps else S
 
     @staticmethod
-    def backward(ctx, grad_S):
+    def backward(ctx, grad_S, *unused):
         (dJdC,) = ctx.saved_tensors
-        return grad_S * dJdC, None, None, None, None
+        return grad_S.to(dJdC.dtype) * dJdC, None, None, None, None, None
 
 
-def eps_adjoint(C, prob: Problem, EF, EA, scale: float = -2.0):
-    """The Eq. 1 surrogate S(C) (see EpsAdjoint); S.backward() leaves
-    dJ/dC in C.grad."""
-    return EpsAdjoint.apply(C, prob, list(EF), list(EA), scale)
+def eps_adjoint(C, prob: Problem, EF, EA, scale: float = -2.0, with_eps: bool = False):
+    """The Eq. 1 surrogate S(C) (see EpsAdjoint), a float64 0-d tensor;
+    S.backward() leaves dJ/dC in C.grad.  With with_eps, returns (S, eps_hat)
+    from the same fused call (eps_hat is what the next field solve needs)."""
+    return EpsAdjoint.apply(C, prob, list(EF), list(EA), scale, with_eps)
 
 
 class EpsChainMorph(torch.autograd.Function):

@@ -95,10 +95,11 @@ eps_status_t resolve(const eps_problem_t *p, Resolved *r) {
   return EPS_OK;
 }
 
-// Workspace: W [4][nx][ny] | seeds [NSEED][nx][ny] | pd4 [mx][my] | ie2 [mx][my],
-// each 256-byte aligned.
+// Workspace: W [4][nx][ny] | seeds [NSEED][nx][ny] | pd4 [mx][my] | ie2 [mx][my]
+// | epsc [4][nx][ny] (per-column eps values for the Eq. 1 surrogate, used by
+// eps_vjp_surrogate only), each 256-byte aligned.
 struct WsLayout {
-  size_t w, seeds, pd4, ie2, total;
+  size_t w, seeds, pd4, ie2, epsc, total;
 };
 
 WsLayout ws_layout(const Geometry &g) {
@@ -109,7 +110,8 @@ WsLayout ws_layout(const Geometry &g) {
   L.seeds = L.w + align256(sizeof(float) * 4 * cells);
   L.pd4 = L.seeds + align256(sizeof(float) * NSEED * cells);
   L.ie2 = L.pd4 + align256(sizeof(float) * subs);
-  L.total = L.ie2 + align256(sizeof(float) * subs);
+  L.epsc = L.ie2 + align256(sizeof(float) * subs);
+  L.total = L.epsc + align256(sizeof(float) * 4 * cells);
   return L;
 }
 
@@ -177,7 +179,7 @@ eps_status_t sm_count(int *n) {
 // (griddepcontrol.wait) before reading its results.  While profiling, each
 // launch is bracketed by events and launched without overlap.
 eps_status_t launch(const char *name, const void *fn, dim3 grid, size_t smem, void *args,
-                    cudaStream_t s, bool pdl = false) {
+                    cudaStream_t s, bool pdl = false, unsigned block = NTHREADS) {
   eps_status_t st = prepare(fn, smem);
   if (st != EPS_OK) return st;
   ProfRec rec{name, nullptr, nullptr};
@@ -193,7 +195,7 @@ eps_status_t launch(const char *name, const void *fn, dim3 grid, size_t smem, vo
   if (prof && cudaEventRecord(rec.e0, s) != cudaSuccess) return EPS_ERR_CUDA;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(NTHREADS);
+  cfg.blockDim = dim3(block);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -506,13 +508,15 @@ eps_status_t stencil_form(const Geometry &g, StencilForm *f, long *blocks) {
 }
 
 eps_status_t run_seeds_one(const Geometry &g, const float *W, float *seeds, int *err,
-                           cudaStream_t s) {
+                           cudaStream_t s, const float *epsc = nullptr, double *S = nullptr) {
   SeedsArgs sa;
   std::memset(&sa, 0, sizeof(sa));
   sa.n = 1;
   sa.ncol = (long)g.nx * g.ny;
   sa.r[0] = SeedsRegion{0, sa.ncol, W, seeds};
   sa.err = err;
+  sa.epsc = epsc;
+  sa.S = S;
   return run_seeds(sa, s);
 }
 
@@ -704,19 +708,24 @@ eps_status_t vjp_args(const Resolved &r, const float *C, int32_t n_lambda, int32
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda,
-                     int32_t field_type, const void *const *EF, const void *const *EA,
-                     const float *field_scales, float scale, float *dJdC, float *eps_out,
-                     void *ws, size_t ws_bytes, eps_stream_t stream) {
+// The fused forward + Eq. 1 VJP of eps_vjp; with S non-null also the
+// surrogate S = sum over the J-support voxels of eps_hat * w (zeroed here,
+// accumulated by the stencil or the seeds kernel).
+eps_status_t vjp_fused(const eps_problem_t *prob, const float *C, int32_t n_lambda,
+                       int32_t field_type, const void *const *EF, const void *const *EA,
+                       const float *field_scales, float scale, float *dJdC, float *eps_out,
+                       double *S, void *ws, size_t ws_bytes, cudaStream_t s) {
   Resolved r;
   eps_status_t st = resolve(prob, &r);
   if (st != EPS_OK) return st;
   bool skip = false;
   st = vjp_args(r, C, n_lambda, field_type, EF, EA, field_scales, scale, dJdC, eps_out, ws,
                 ws_bytes, &skip);
-  if (st != EPS_OK || skip) return st;
+  if (st != EPS_OK) return st;
+  if (S && cudaMemsetAsync(S, 0, sizeof(double), s) != cudaSuccess) return EPS_ERR_CUDA;
+  if (skip) return EPS_OK;
   int *err = nullptr;
   if ((st = error_flag_ptr(&err)) != EPS_OK) return st;
 
@@ -725,7 +734,7 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   float *seeds = (float *)((char *)ws + L.seeds);
   float *pd4 = (float *)((char *)ws + L.pd4);
   float *ie2 = (float *)((char *)ws + L.ie2);
-  cudaStream_t s = (cudaStream_t)stream;
+  float *epsc = (float *)((char *)ws + L.epsc);
 
   // 1. Eq. 1 column sums (streaming over the J-support planes)
   ContractArgs ca;
@@ -773,6 +782,10 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
   fa.r.defer_seeds = form.defer;
   fa.r.pd4 = pd4;
   fa.r.ie2 = ie2;
+  if (S) {
+    fa.r.S = form.defer ? nullptr : S;
+    fa.r.epsc = form.defer ? epsc : nullptr;
+  }
   const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
   const size_t smem =
       fwd_smem(kf, r.g, eps_out ? std::min(3, form.stage_comps) : 0, &fa.r.stage_floats);
@@ -780,9 +793,33 @@ eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda
               smem, &fa, s, true);
   if (st != EPS_OK) return st;
   // 3. (seeds-kernel form) seeds = factor * W, once both grids are done
-  if (form.defer == 1 && (st = run_seeds_one(r.g, Wm, seeds, err, s)) != EPS_OK) return st;
+  if (form.defer == 1 &&
+      (st = run_seeds_one(r.g, Wm, seeds, err, s, S ? epsc : nullptr, S)) != EPS_OK)
+    return st;
   // 4. transposes down to dJ/dC
   return run_scatter(r, seeds, pd4, ie2, dJdC, err, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda,
+                     int32_t field_type, const void *const *EF, const void *const *EA,
+                     const float *field_scales, float scale, float *dJdC, float *eps_out,
+                     void *ws, size_t ws_bytes, eps_stream_t stream) {
+  return vjp_fused(prob, C, n_lambda, field_type, EF, EA, field_scales, scale, dJdC, eps_out,
+                   nullptr, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+eps_status_t eps_vjp_surrogate(const eps_problem_t *prob, const float *C, int32_t n_lambda,
+                               int32_t field_type, const void *const *EF, const void *const *EA,
+                               const float *field_scales, float scale, float *dJdC,
+                               float *eps_out, double *S, void *ws, size_t ws_bytes,
+                               eps_stream_t stream) {
+  if (!S || !aligned(S, 8)) return EPS_ERR_INVALID_ARG;
+  return vjp_fused(prob, C, n_lambda, field_type, EF, EA, field_scales, scale, dJdC, eps_out, S,
+                   ws, ws_bytes, (cudaStream_t)stream);
 }
 
 eps_status_t eps_vjp_real(const eps_problem_t *prob, const float *C, const float *G, float *dJdC,

@@ -25,7 +25,9 @@ void *g_static_addr[MAX_DEVICES];   // device address of the array, per device
 
 // Device address of the scratch array on the current device.  The host-side
 // name of a __device__ array is only a stand-in, so the address is looked up
-// once per device with that device current and cached.
+// once per device with that device current and cached for the rest of the
+// process (valid in the device's primary context; a cudaDeviceReset() would
+// leave a stale entry, which the header rules out).
 eps_status_t static_scratch(void **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return EPS_ERR_CUDA;

@@ -91,6 +91,13 @@ struct FwdRegion {
   float *seeds;                  // [NSEED][nx][ny]
   float *pd4;                    // [mx][my] P'(u) (eps_core - eps_clad) / 4
   float *ie2;                    // [mx][my] 1 / eps^2
+  // Eq. 1 surrogate S = sum over the J-support voxels of eps_hat * w (null:
+  // not requested).  A tile that waits for the contraction adds its
+  // columns' eps . W to *S itself; with defer_seeds it writes the column
+  // values (eps_xx, eps_yy, eps_zz inside, eps_zz on the faces) to epsc
+  // [4][nx][ny] and the seeds kernel adds them up.
+  double *S;
+  float *epsc;
 };
 
 // Seeds kernel: regions laid end to end in one column space.
@@ -104,8 +111,31 @@ struct SeedsArgs {
   int n;
   long ncol;
   int *err;                      // error flag (debug bounds checks)
+  // Eq. 1 surrogate (single-region calls; null: not requested): *S +=
+  // sum over columns of epsc . W, epsc [4][nx][ny] from the stencil
+  const float *epsc;
+  double *S;
   SeedsRegion r[EPS_MAX_BATCH];
 };
+
+// Sum of v over the block (NTHREADS threads), added to *S by thread 0.  Every
+// thread of the block must call it.  FP64 from the per-thread values on, so
+// that the order of the block's and the grid's additions hardly matters.
+__device__ __forceinline__ void block_add_to(double *S, double v) {
+  __shared__ double part[NTHREADS / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();   // part[] may still be read by an earlier call
+  if (lane == 0) part[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NTHREADS / 32; ++w) t += part[w];
+    atomicAdd(S, t);
+  }
+}
 
 // Kernel arguments end with the conic weights, a dense (2 RP1 - 1)^2 box,
 // row-major.  Each kernel takes the struct with exactly its box (NW = (2 RP1

@@ -407,6 +407,7 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
   }
   float Wx = 1.f, Wy = 1.f, Wzi = 0.f, Wzf = 1.f;
   if (!rg.defer_seeds) griddep_wait();   // the contraction grid has completed
+  double s_col = 0.0;                    // this column's eps . W (Eq. 1 surrogate)
   if (valid && EPSC_IN_BOUNDS((size_t)ci * g.ny + cj, 1, (size_t)g.nx * g.ny, a.err)) {
     const size_t plane = (size_t)g.nx * g.ny;
     if (!rg.defer_seeds) {
@@ -415,6 +416,15 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
       Wy = wc[1 * plane];
       Wzi = wc[2 * plane];
       Wzf = wc[3 * plane];
+      // eps_hat is constant along z on each support run: eps_xx, eps_yy on
+      // planes k0+1 .. k0+nk, eps_zz = A_z inside, ezf on the two faces
+      s_col = fmaf(ex, Wx, ey * Wy) + fmaf(ezi, Wzi, ezf * Wzf);
+    } else if (rg.epsc) {
+      float *ec = rg.epsc + (size_t)ci * g.ny + cj;
+      ec[0 * plane] = ex;
+      ec[1 * plane] = ey;
+      ec[2 * plane] = ezi;
+      ec[3 * plane] = ezf;
     }
     float *sd = rg.seeds + (size_t)ci * g.ny + cj;
     sd[S_DAX * plane] = fAx * Wx;
@@ -428,6 +438,7 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
     if (!rg.defer_seeds) sd[S_DAZ * plane] = Wzi;
     sd[S_DHZ * plane] = fHz * Wzf;
   }
+  if (rg.S && !rg.defer_seeds) block_add_to(rg.S, s_col);   // uniform over the block
   if (bulk_pending && tid == 0) bulk_wait_all();
 }
 

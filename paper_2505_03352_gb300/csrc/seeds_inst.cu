@@ -5,13 +5,22 @@
 // W_x; the same per W_y; dJ/dH_z per W_zf); dJ/dA_z is W_zi itself.  This
 // kernel runs once both the contraction and the stencil have completed
 // (ordinary stream order) and turns the factors into seeds in place, over
-// all regions of a call (one region for the single-region calls).
+// all regions of a call (one region for the single-region calls).  When the
+// Eq. 1 surrogate is requested (single-region calls) it also adds
+// sum over columns of eps_col . W to *S, from the per-column eps values the
+// stencil left in epsc.
 #include "epsc_launch.h"
 
 namespace epsc {
 
 __device__ __forceinline__ float4 mul4(float4 v, float4 w) {
   return make_float4(v.x * w.x, v.y * w.y, v.z * w.z, v.w * w.w);
+}
+
+// sum of the four products (FP32: a handful of terms per thread; the block
+// and grid sums that follow run in FP64)
+__device__ __forceinline__ float dot4(float4 v, float4 w) {
+  return fmaf(v.x, w.x, v.y * w.y) + fmaf(v.z, w.z, v.w * w.w);
 }
 
 __global__ void __launch_bounds__(NTHREADS) seeds_kernel(const __grid_constant__ SeedsArgs a) {
@@ -25,10 +34,14 @@ __global__ void __launch_bounds__(NTHREADS) seeds_kernel(const __grid_constant__
     const SeedsRegion &rg = a.r[0];
     const long p4 = rg.ncol >> 2;
     const float4 *W = reinterpret_cast<const float4 *>(rg.W);
+    const float4 *E = reinterpret_cast<const float4 *>(a.epsc);
     float4 *s = reinterpret_cast<float4 *>(rg.seeds);
+    double sum = 0.0;
     for (long q = (long)blockIdx.x * NTHREADS + threadIdx.x; q < p4; q += (long)gridDim.x * NTHREADS) {
       const float4 Wx = __ldg(W + q), Wy = __ldg(W + p4 + q);
       const float4 Wzi = __ldg(W + 2 * p4 + q), Wzf = __ldg(W + 3 * p4 + q);
+      if (a.S) sum += dot4(__ldg(E + q), Wx) + dot4(__ldg(E + p4 + q), Wy) +
+                      dot4(__ldg(E + 2 * p4 + q), Wzi) + dot4(__ldg(E + 3 * p4 + q), Wzf);
       s[S_DAX * p4 + q] = mul4(s[S_DAX * p4 + q], Wx);
       s[S_DHX * p4 + q] = mul4(s[S_DHX * p4 + q], Wx);
       s[S_GXX * p4 + q] = mul4(s[S_GXX * p4 + q], Wx);
@@ -40,8 +53,10 @@ __global__ void __launch_bounds__(NTHREADS) seeds_kernel(const __grid_constant__
       s[S_DAZ * p4 + q] = Wzi;
       s[S_DHZ * p4 + q] = mul4(s[S_DHZ * p4 + q], Wzf);
     }
+    if (a.S) block_add_to(a.S, sum);   // uniform over the grid
     return;
   }
+  double sum = 0.0;
   for (long c = (long)blockIdx.x * NTHREADS + threadIdx.x; c < a.ncol; c += (long)gridDim.x * NTHREADS) {
     int k = 0;
     while (k + 1 < a.n && c >= a.r[k + 1].col_start) ++k;
@@ -61,7 +76,12 @@ __global__ void __launch_bounds__(NTHREADS) seeds_kernel(const __grid_constant__
     s[S_GYY * p] *= Wy;
     s[S_DAZ * p] = Wzi;
     s[S_DHZ * p] *= Wzf;
+    if (a.S && a.n == 1) {
+      const float *e = a.epsc + j;
+      sum += fmaf(e[0], Wx, e[p] * Wy) + fmaf(e[2 * p], Wzi, e[3 * p] * Wzf);
+    }
   }
+  if (a.S) block_add_to(a.S, sum);
 }
 
 const void *seeds_entry() { return (const void *)&seeds_kernel; }

@@ -96,6 +96,9 @@ _PROTOS = {
     "eps_forward": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP]),
     "eps_vjp": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, ctypes.c_int32, ctypes.c_int32,
                                _VP, _VP, _VP, ctypes.c_float, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "eps_vjp_surrogate": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, ctypes.c_int32,
+                                         ctypes.c_int32, _VP, _VP, _VP, ctypes.c_float, _VP, _VP,
+                                         _VP, _VP, ctypes.c_size_t, _VP]),
     "eps_vjp_real": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), _VP, _VP, _VP, _VP,
                                     ctypes.c_size_t, _VP]),
     "eps_sync_status": (ctypes.c_int, [_VP]),
@@ -331,6 +334,34 @@ def eps_vjp(prob: Problem, C, EF, EA, scale: float = -2.0, dJdC=None, eps_out=No
                          _ptr(dJdC), _ptr(eps_out), _ptr(ws), ws.numel(), _stream(stream, dev)),
            "eps_vjp")
     return (dJdC, eps_out) if ret_eps else dJdC
+
+
+def eps_vjp_surrogate(prob: Problem, C, EF, EA, scale: float = -2.0, dJdC=None, eps_out=None,
+                      S=None, field_type: int = EPS_FIELD_C64, field_scales=None, ws=None,
+                      stream=None):
+    """eps_vjp plus the Eq. 1 surrogate S = sum over the J-support voxels of
+    eps_hat * scale Re(sum_l E_F,l E_A,l), whose gradient is dJ/dC.  S is a
+    float64 0-d device tensor (allocated if not given).  Returns
+    (dJdC, S) or, with eps_out, (dJdC, eps_out, S)."""
+    import torch
+    _need(C, (prob.mx, prob.my), torch.float32, "C")
+    dev = C.device
+    nl, ef, ea = _field_ptrs(prob, EF, EA, field_type, dev)
+    fs = _scales(field_scales, nl)
+    if dJdC is None:
+        dJdC = torch.empty((prob.mx, prob.my), dtype=torch.float32, device=dev)
+    _need(dJdC, (prob.mx, prob.my), torch.float32, "dJdC", dev)
+    if S is None:
+        S = torch.empty((), dtype=torch.float64, device=dev)
+    _need(S, (), torch.float64, "S", dev)
+    ret_eps, eps_out = _eps_out(prob, eps_out, dev)
+    ws = _workspace(prob, nl, ws, dev)
+    p = prob.c_struct()
+    _check(lib().eps_vjp_surrogate(ctypes.byref(p), _ptr(C), nl, field_type, ef, ea, fs,
+                                   float(scale), _ptr(dJdC), _ptr(eps_out), _ptr(S), _ptr(ws),
+                                   ws.numel(), _stream(stream, dev)),
+           "eps_vjp_surrogate")
+    return (dJdC, eps_out, S) if ret_eps else (dJdC, S)
 
 
 def _flatten(x):

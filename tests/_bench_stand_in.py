@@ -78,7 +78,8 @@ def main():
     torch.Tensor.pin_memory = lambda self, *a, **k: self
     # the recorder writes no outputs: hand out zeroed memory instead of garbage
     _zeros, _zeros_like = torch.zeros, torch.zeros_like
-    torch.empty = lambda *a, **k: _zeros(*a, **k)
+    # (no pinned host memory without a driver: pin_memory=True is dropped)
+    torch.empty = lambda *a, **k: _zeros(*a, **{n: v for n, v in k.items() if n != "pin_memory"})
     torch.empty_like = lambda *a, **k: _zeros_like(*a, **k)
 
 

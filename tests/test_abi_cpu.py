@@ -69,8 +69,9 @@ def test_workspace_size_layout(L):
     w = 4 * 300 * 300 * 4          # Eq. 1 column sums
     seeds = 10 * 300 * 300 * 4     # adjoint seeds per Yee column
     sub = 600 * 600 * 4            # per-subpixel adjoint factors (two maps)
+    epsc = 4 * 300 * 300 * 4       # per-column eps values for the Eq. 1 surrogate
     al = lambda b: (b + 255) // 256 * 256
-    assert n == al(w) + al(seeds) + 2 * al(sub)
+    assert n == al(w) + al(seeds) + 2 * al(sub) + al(epsc)
     assert ec.eps_workspace_size(prob(mx=0)) == 0
 
 
@@ -120,6 +121,13 @@ def test_entry_points_reject_null_pointers_before_launch(L):
     # non-finite scale
     assert L.eps_vjp(P, None, 1, 0, None, None, None, float("nan"), None, None, None, 0,
                      None) == 1
+    # the surrogate's value pointer: NULL or not 8-byte aligned
+    fake = ctypes.c_void_p(0x10000)
+    arr = (ctypes.c_void_p * 1)(fake)
+    assert L.eps_vjp_surrogate(P, fake, 1, 0, arr, arr, None, -2.0, fake, None, None, fake,
+                               1 << 30, None) == 1
+    assert L.eps_vjp_surrogate(P, fake, 1, 0, arr, arr, None, -2.0, fake, None,
+                               ctypes.c_void_p(0x10004), fake, 1 << 30, None) == 1
 
 
 def test_workspace_too_small_is_reported(L):

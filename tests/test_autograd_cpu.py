@@ -1,9 +1,12 @@
-"""The Eq. 1 surrogate EpsAdjoint, without a GPU: its fused library call is
-replaced by the FP64 oracle (eps_hat and J^T w of the same inputs), so that
-the wrapper's own arithmetic is what is tested.
+"""The Eq. 1 surrogate EpsAdjoint, without a GPU: its fused library call
+(eps_vjp_surrogate) is replaced by the FP64 oracle (eps_hat, J^T w and the
+sum of eps_hat * w over the J-support voxels, of the same inputs), so that
+the wrapper's own plumbing is what is tested, and the surrogate's
+definition is pinned against Eq. 1 by finite differences.
 
-- S(C) equals scale * sum eps_hat * Re(sum_l E_F,l E_A,l), with the product
-  unconjugated;
+- S(C) equals scale * sum over the J-support voxels (Ex/Ey planes
+  k0+1 .. k0+nk, Ez planes k0 .. k0+nk) of eps_hat * Re(sum_l E_F,l E_A,l),
+  with the product unconjugated;
 - S.backward() leaves the call's dJ/dC, times the incoming gradient, in
   C.grad, and the fields get none;
 - the gradient of S is Eq. 1: torch.autograd.gradcheck compares it with
@@ -25,23 +28,34 @@ def _oracle_problem(p):
                        slab_k0=p.slab_k0, bc=p.bc)
 
 
+def _support_mask(o):
+    # the voxels whose eps_hat depends on C (z rules of Sec. 3's extrusion)
+    m = np.zeros((3, o.nx, o.ny, o.nz), dtype=bool)
+    k0, nk = o.k0, o.slab_nk
+    m[0:2, :, :, k0 + 1:k0 + nk + 1] = True
+    m[2, :, :, k0:k0 + nk + 1] = True
+    return m
+
+
 @pytest.fixture
 def oracle_call(monkeypatch):
-    """eps_vjp(prob, C, EF, EA, scale, eps_out=True) answered by the oracle."""
+    """eps_vjp_surrogate(prob, C, EF, EA, scale, eps_out) answered by the
+    oracle."""
     calls = []
 
     def fused(prob, C, EF, EA, scale=-2.0, eps_out=None, **kw):
-        assert eps_out is True
         o = _oracle_problem(prob)
         Cn = C.detach().numpy().astype(np.float64)
         w = np.zeros((3, o.nx, o.ny, o.nz))
         for ef, ea in zip(EF, EA):
             w += (ef.numpy() * ea.numpy()).real
         calls.append(len(EF))
-        return (torch.from_numpy(orc.vjp_real(o, Cn, scale * w)),
-                torch.from_numpy(orc.eps_hat(o, Cn)))
+        e = orc.eps_hat(o, Cn)
+        S = torch.tensor(float(np.sum((e * scale * w)[_support_mask(o)])), dtype=torch.float64)
+        g = torch.from_numpy(orc.vjp_real(o, Cn, scale * w))
+        return (g, torch.from_numpy(e), S) if eps_out is True else (g, S)
 
-    monkeypatch.setattr(ag, "eps_vjp", fused)
+    monkeypatch.setattr(ag, "eps_vjp_surrogate", fused)
     return calls
 
 
@@ -62,15 +76,24 @@ def _inputs(seed, n_lambda=2):
 def test_surrogate_value_and_gradient(oracle_call):
     C, EF, EA = _inputs(1)
     C.requires_grad_(True)
-    S = ag.eps_adjoint(C, P, EF, EA, scale=-2.0)
+    S, eps = ag.eps_adjoint(C, P, EF, EA, scale=-2.0, with_eps=True)
+    assert S.dtype == torch.float64 and not eps.requires_grad
     o = _oracle_problem(P)
     e = orc.eps_hat(o, C.detach().numpy())
+    np.testing.assert_array_equal(eps.numpy(), e)
     w = sum((ef.numpy() * ea.numpy()).real for ef, ea in zip(EF, EA))
-    assert S.item() == pytest.approx(-2.0 * float(np.sum(e * w)), rel=1e-12)
+    assert S.item() == pytest.approx(-2.0 * float(np.sum((e * w)[_support_mask(o)])), rel=1e-12)
+    # the cladding voxels hold eps_clad whatever C is: summing over every
+    # voxel instead changes S by a constant only
+    full = -2.0 * float(np.sum(e * w))
+    e2 = orc.eps_hat(o, C.detach().numpy() * 0.5)
+    S2 = ag.eps_adjoint(C.detach() * 0.5, P, EF, EA)
+    full2 = -2.0 * float(np.sum(e2 * w))
+    assert (full - S.item()) == pytest.approx(full2 - S2.item(), rel=1e-10)
     (3.0 * S).backward()
     ref = orc.vjp_fields(o, C.detach().numpy(), [x.numpy() for x in EF], [x.numpy() for x in EA])
     np.testing.assert_allclose(C.grad.numpy(), 3.0 * ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
-    assert oracle_call == [2]
+    assert oracle_call == [2, 2]
 
 
 def test_surrogate_gradient_is_eq1_by_central_differences(oracle_call):

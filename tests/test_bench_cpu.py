@@ -9,6 +9,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 import bench
@@ -69,15 +70,47 @@ def test_reference_arm_prints_one_json_line():
 
 def test_cpu_baseline_times_the_oracle_on_a_bounded_sample():
     w = synth.WORKLOADS[1]
-    cpu = bench.cpu_baseline(w, budget_s=0.5)
+    C = synth.controls(w)
+    EF, EA = synth.fields(w)
+    cpu, kept = bench.cpu_baseline(w, C, EF, EA, budget_s=0.5, keep=1)
     assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["unit"] == bench.UNIT
     assert cpu["value"] > 0 and 0 < cpu["seconds"] < 60
     assert w.name in cpu["sample"]
+    # the kept result is the oracle's own: the error of the oracle against
+    # itself is zero, and a perturbed copy shows its perturbation
+    (a0, b0, win, g_ref, e_ref), = kept
+    err = bench.oracle_errors(w, kept, g_ref.astype(np.float32), e_ref.astype(np.float32))
+    assert err["dJdC_max_abs_err_over_max_abs_oracle"] < 1e-6
+    assert err["eps_hat_max_rel_err"] < 1e-6
+    bumped = g_ref.copy()
+    bumped[3, 5] += 0.01 * np.max(np.abs(g_ref))
+    assert abs(bench.oracle_errors(w, kept, bumped)["dJdC_max_abs_err_over_max_abs_oracle"]
+               - 0.01) < 1e-9
     allc = cpu["all_cores"]
     from oracle import timing_pool
     assert allc["cores"] == timing_pool.default_workers() and allc["value"] > 0, allc
     assert 1 <= timing_pool.default_workers() <= 32
     assert timing_pool.default_workers(per_worker_bytes=1 << 50) == 1     # memory caps the pool
+
+
+def test_cpu_baseline_windows_and_their_interiors():
+    # window mode: seeded windows of a larger problem, and the error helper
+    # compares only window interiors (a margin of 2 ceil(R) + 8 subpixels
+    # from every window edge inside the region)
+    import dataclasses
+    w = dataclasses.replace(synth.WORKLOADS[2], mx=160, my=160, name="cfg2_crop160")
+    C = synth.controls(w)
+    EF, EA = synth.fields(w, 1)
+    cpu, kept = bench.cpu_baseline(w, C, EF, EA, budget_s=0.2, window=64, max_windows=2,
+                                   all_cores_reps=0, keep=2)
+    assert "windows of 64 x 64 controls" in cpu["sample"] and len(kept) >= 1
+    from oracle import epschain_oracle as orc
+    op = orc.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
+    g_full = orc.vjp_fields(op, C, EF, EA)
+    e_full = orc.eps_hat(op, C)
+    err = bench.oracle_errors(w, kept, g_full, e_full)
+    assert err["dJdC_max_abs_err_over_max_abs_oracle"] < 1e-12
+    assert err["eps_hat_max_rel_err"] < 1e-12
 
 
 def test_gpu_arm_runs_end_to_end_on_a_stand_in_device():
@@ -98,14 +131,20 @@ def test_gpu_arm_runs_end_to_end_on_a_stand_in_device():
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(d["roofline"])
     rf = d["roofline"]
     if rf["traffic"]:                       # the committed capture matches the kernel source
-        assert rf["layout_ceiling_frac"] == round(bench.contraction_bytes(synth.WORKLOADS[2], 1)
+        assert rf["layout_ceiling_frac"] == round(rf["algorithmic_bytes_per_launch"]
                                                   / rf["traffic"], 4)
         assert rf["dram_frac"] > 0
+    assert d["config"]["workload"] == synth.WORKLOADS[5].name and d["config"]["wavelengths"] == 8
     assert {"value", "unit", "cores", "kind", "sample"} <= set(d["cpu_baseline"])
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] > 0
+    assert "dJdC_max_abs_err_over_max_abs_oracle" in d["accuracy_vs_fp64_oracle"]
     c5 = d["variants"]["cfg5_precision_8wavelengths"]
-    assert "dJdC_max_dev_vs_fp32_path" in c5["bf16"] and "dJdC_max_dev_vs_fp32_path" in c5["fp16"]
-    assert set(d["variants"]) >= {"cfg3_fp32_3wavelengths", "cfg4_batched_64_regions",
-                                  "cfg5_precision_8wavelengths", "cfg2_morphology", "optimizer_step",
-                                  "coarse_controls", "forward_tensor_cfg2", "autograd_cfg3"}
+    for ft in ("bf16", "fp16"):
+        assert "dJdC_max_dev_vs_fp32_path" in c5[ft] and "vs_fp64_oracle" in c5[ft]
+        assert "packed_contraction" in c5[ft]
+    assert "dJdC_max_abs_err_over_max_abs_oracle" in c5["fp32"]
+    assert set(d["variants"]) >= {"cfg2_fp32_1wavelength", "cfg3_fp32_3wavelengths",
+                                  "cfg4_batched_64_regions", "cfg5_precision_8wavelengths",
+                                  "cfg2_morphology", "optimizer_step", "coarse_controls",
+                                  "forward_tensor_cfg2", "autograd_cfg3"}

@@ -1,9 +1,22 @@
 """eps_vjp_static, the entry point that allocates nothing, against eps_vjp.
 
-This file is collected last on purpose: if it fails, a run that stops at the
-first failure has already run every other test.  It calls the C ABI directly
-(ctypes), twice in a row on the same inputs, and compares with eps_vjp given
-a workspace, within the parity tolerances of the other GPU tests.
+Some callers cannot allocate device memory where they need the gradient: a
+framework whose memory pool already holds the whole GPU, or a loop that may
+not call cudaMalloc after start-up because it can synchronise the device.
+eps_vjp_static serves them from one static scratch array per GPU.
+
+This file sorts after every other test file, so a run that stops at the
+first failure has run the rest of the suite before it.  It calls the C ABI
+directly (ctypes) and compares with eps_vjp given a caller workspace that
+is filled with NaN first (so the reference itself reads no scratch value it
+did not write), within the parity tolerances of the other GPU tests.  The
+static array keeps the previous call's contents, so before the checked
+calls it is filled by a call on another problem with other inputs; the
+checked problem is then solved twice in a row.  Both launch forms of the
+stencil are covered: a one-wave problem (each tile waits for the field
+contraction and writes its seeds) and a multi-wave one (the stencil writes
+seed factors and a separate kernel multiplies them by the column sums;
+its scatter stages through bulk tensor copies).
 """
 
 import ctypes
@@ -41,22 +54,43 @@ def _static_call(torch, eb, L, prob, C, EF, EA, dJdC, eps):
                             -2.0, dJdC.data_ptr(), eps.data_ptr(), stream)
 
 
-def test_static_scratch_matches_workspace_version_twice():
+def _inputs(torch, ec, mx, nz, radius, beta, seed):
+    prob = ec.Problem(mx=mx, my=mx, nz=nz, radius=radius, beta=beta)
+    C = torch.from_numpy(synth.soi_layout(mx, mx, seed)).cuda()
+    shape = (3, prob.nx, prob.ny, nz)
+    EF = torch.from_numpy(synth.complex_field(shape, seed + 1)).cuda()
+    EA = torch.from_numpy(synth.complex_field(shape, seed + 2)).cuda()
+    return prob, C, EF, EA
+
+
+# (controls per side, nz): 600 x 600 is one wave of stencil tiles on a
+# 152-SM GB300 (380 tiles); 760 x 760 is two (576 tiles), with a 14 MiB
+# workspace, inside the static array
+@pytest.mark.parametrize("mx,nz", [(600, 24), (760, 32)], ids=["one_wave", "multi_wave"])
+def test_static_scratch_matches_workspace_version_twice(mx, nz):
     torch, ec, eb, L = _setup()
-    w = synth.WORKLOADS[2]
-    prob = ec.Problem(mx=w.mx, my=w.my, nz=w.nz, radius=w.radius, beta=w.beta)
-    C = torch.from_numpy(synth.controls(w)).cuda()
-    EF, EA = synth.fields(w)
-    EFd = torch.from_numpy(EF[0]).cuda()
-    EAd = torch.from_numpy(EA[0]).cuda()
-    ref_g, ref_e = ec.eps_vjp(prob, C, [EFd], [EAd], eps_out=True)
+    prob, C, EF, EA = _inputs(torch, ec, mx, nz, 6.0, 16.0, 1002)
+    need = ec.eps_workspace_size(prob)
+    assert need <= 16 * 1024 * 1024
+    ws = torch.full((need // 4 + 64,), float("nan"), device="cuda").view(torch.uint8)
+    ref_g, ref_e = ec.eps_vjp(prob, C, [EF], [EA], eps_out=True, ws=ws[:need])
     ec.eps_sync_status()
     ref_g, ref_e = ref_g.cpu().numpy(), ref_e.cpu().numpy()
+    assert np.isfinite(ref_g).all() and np.isfinite(ref_e).all()
     scale = np.max(np.abs(ref_g))
+
+    # another problem (other size, depth, radius, beta and inputs) first, so
+    # the static array holds its data when the checked calls begin
+    p2, C2, EF2, EA2 = _inputs(torch, ec, 520, 16, 3.0, 8.0, 77)
+    g2 = torch.empty((p2.mx, p2.my), device="cuda")
+    e2 = torch.empty((3, p2.nx, p2.ny, p2.nz), device="cuda")
+    assert _static_call(torch, eb, L, p2, C2, EF2, EA2, g2, e2) == eb.EPS_OK
+    ec.eps_sync_status()
+
     for _ in range(2):
-        dJdC = torch.full((w.mx, w.my), float("nan"), device="cuda")
-        eps = torch.full((3, w.nx, w.ny, w.nz), float("nan"), device="cuda")
-        st = _static_call(torch, eb, L, prob, C, EFd, EAd, dJdC, eps)
+        dJdC = torch.full((prob.mx, prob.my), float("nan"), device="cuda")
+        eps = torch.full((3, prob.nx, prob.ny, prob.nz), float("nan"), device="cuda")
+        st = _static_call(torch, eb, L, prob, C, EF, EA, dJdC, eps)
         assert st == eb.EPS_OK, eb.STATUS_NAMES.get(st, st)
         ec.eps_sync_status()
         g, e = dJdC.cpu().numpy(), eps.cpu().numpy()
