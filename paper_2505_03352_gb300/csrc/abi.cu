@@ -436,6 +436,13 @@ eps_status_t run_contract_tma_real(const Geometry &g, const float *G, float *Wm,
                 &ta, s);
 }
 
+// Launch shape of the bulk-copy packed contraction (swept at the 3000 x
+// 3000, eight-wavelength BF16 call: 2 x 2 stages of 128 columns, with the
+// stencil beside it, 1.23 ms; 2 x 3 stages 1.35 ms; the register-load
+// kernel, which fills every SM slot, 1.41 ms).
+constexpr int PACKED_BLOCKS_PER_SM = 2;
+constexpr int PACKED_NSTAGE = 2;
+
 // Packed planes per column (multiple of 4) and bytes of one packed field.
 int packed_planes(const Geometry &g) { return (g.nk + 1 + 3) & ~3; }
 size_t packed_bytes(const Geometry &g) {
@@ -465,6 +472,20 @@ eps_status_t run_contract_packed(const Geometry &g, int n_lambda, int type, cons
   eps_status_t st = sm_count(&nsm);
   if (st != EPS_OK) return st;
   const long ncol = (long)g.nx * g.ny;
+  bool bulk = true;
+  for (int l = 0; l < n_lambda; ++l) bulk = bulk && aligned(EF[l], 16) && aligned(EA[l], 16);
+  if (bulk && n_lambda > 0) {
+    // ring of PACKED_NSTAGE stages of 6 x PK_BY x 4 np bytes (37 KB at nk =
+    // 11) in PACKED_BLOCKS_PER_SM blocks per SM: about 74 KB per block, so
+    // stencil blocks (32 KB with one eps_hat component staged per round)
+    // still fit beside the two
+    pa.nstage = PACKED_NSTAGE;
+    const size_t smem = (size_t)PACKED_NSTAGE * 6 * PK_BY * pa.np * 4 + 128;
+    const long nchunks = (ncol + PK_BY - 1) / PK_BY;
+    const long blocks = std::max<long>(1, std::min<long>(nchunks, (long)nsm * PACKED_BLOCKS_PER_SM));
+    return launch("eps_vjp_contract_packed", contract_packed_bulk_entry(), dim3((unsigned)blocks),
+                  smem, &pa, s, false, PK_THREADS);
+  }
   const long blocks = std::max<long>(1, std::min<long>((ncol + NTHREADS - 1) / NTHREADS, (long)nsm * 8));
   return launch("eps_vjp_contract_packed", contract_packed_entry(), dim3((unsigned)blocks), 0, &pa, s);
 }
@@ -495,7 +516,12 @@ struct StencilForm {
 };
 constexpr int ONE_WAVE_TILES_PER_SM = 3;
 constexpr StencilForm FORM_ONE_WAVE{0, 3};
-constexpr StencilForm FORM_MULTI_WAVE{1, 3};
+// Multi-wave problems stage one eps_hat component per round: 32 KB of shared
+// memory at nz = 32 instead of 98 KB, so four stencil blocks fit on an SM
+// (or some beside the field contraction).  Measured: the 2000 x 2000,
+// three-wavelength call 526 -> 519 us, the 3000 x 3000 eight-wavelength
+// call 2.41 -> 2.39 ms (FP32) and 1.44 -> 1.23 ms (BF16).
+constexpr StencilForm FORM_MULTI_WAVE{1, 1};
 
 eps_status_t stencil_form(const Geometry &g, StencilForm *f, long *blocks) {
   int nsm = 0;
@@ -665,7 +691,10 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps, 
   fa.r.eps = eps;
   fa.r.offdiag = od ? offdiag : nullptr;
   const KernelEntry k = fwd_entry(r.rp1, r.g.bc);
-  const size_t smem = fwd_smem(k, r.g, od ? 5 : 3, &fa.r.stage_floats);
+  // one eps_hat component staged per round (the stencil's own buffers are
+  // the larger part then): more resident blocks; the 2000 x 2000 forward
+  // went from 197 to 150 us against three components per round
+  const size_t smem = fwd_smem(k, r.g, od ? 5 : 1, &fa.r.stage_floats);
   return launch("eps_forward", k.fn, dim3((unsigned)fwd_ntiles(r.g)), smem, &fa, (cudaStream_t)stream);
 }
 

@@ -16,6 +16,7 @@ const void *contract_tma_entry(int n_lambda) {
   if (n_lambda <= 1) return (const void *)&contract_tma_kernel<TMA_NSTAGE, 2>;
   if (n_lambda <= 2) return (const void *)&contract_tma_kernel<TMA_NSTAGE, 4>;
   if (n_lambda <= 4) return (const void *)&contract_tma_kernel<TMA_NSTAGE, 8>;
+  if (n_lambda <= 8) return (const void *)&contract_tma_kernel<TMA_NSTAGE, 16>;
   return (const void *)&contract_tma_kernel<TMA_NSTAGE, EPS_MAX_LAMBDA * 2>;
 }
 

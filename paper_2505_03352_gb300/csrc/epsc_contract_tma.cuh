@@ -26,7 +26,7 @@ constexpr int TMA_BY = 32;        // columns per box
 constexpr int TMA_NSTAGE = 2; // ring depth
 constexpr int TMA_BX_MAX = 64;    // floats per box row (support window)
 
-// The tensor maps come last: the kernel is instantiated for 2, 4, 8 or
+// The tensor maps come last: the kernel is instantiated for 2, 4, 8, 16 or
 // 2 EPS_MAX_LAMBDA maps and takes only its own count; the host fills the
 // full-size struct and the launch copies the kernel's parameter bytes, a
 // common prefix (smaller parameter blocks launch faster).

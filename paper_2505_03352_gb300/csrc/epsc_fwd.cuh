@@ -370,8 +370,11 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
       }
     }
   }
+  // Before the block may leave (or the next tile reuse shared memory) its
+  // bulk stores must have read the staging area; their global writes
+  // complete on their own and are visible once the grid has completed.
   if (rg.mode == MODE_FWD) {
-    if (bulk_pending && tid == 0) bulk_wait_all();
+    if (bulk_pending && tid == 0) bulk_wait_read();
     return;
   }
 
@@ -439,21 +442,24 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
     sd[S_DHZ * plane] = fHz * Wzf;
   }
   if (rg.S && !rg.defer_seeds) block_add_to(rg.S, s_col);   // uniform over the block
-  if (bulk_pending && tid == 0) bulk_wait_all();
+  if (bulk_pending && tid == 0) bulk_wait_read();
 }
 
 // Single-region stencil over a 1-D grid: block b takes tiles b,
 // b + gridDim.x, ... of the row-major tile grid (one tile per block when the
 // grid covers them all).
+// (radius classes up to 8: at most 64 registers a thread, so four blocks fit
+// on an SM when the eps_hat staging is one component per round; larger
+// classes would spill at that bound and keep three)
 template <int RP1, int BC>
-__global__ void __launch_bounds__(NTHREADS, 3) fwd_kernel(const __grid_constant__ FwdArgsR<RP1> a) {
+__global__ void __launch_bounds__(NTHREADS, (RP1 <= 8 ? 4 : 3)) fwd_kernel(const __grid_constant__ FwdArgsR<RP1> a) {
   const Geometry &g = a.r.g;
   const int tiles_j = (g.ny + TJ - 1) / TJ;
   const int ntiles = tiles_j * ((g.nx + TI - 1) / TI);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int ti = t / tiles_j;
     fwd_tile<RP1, BC>(a, a.r, ti * TI, (t - ti * tiles_j) * TJ);
-    __syncthreads();   // the next tile reuses shared memory (bulk stores have drained)
+    __syncthreads();   // the next tile reuses shared memory (bulk stores have read it)
   }
 }
 

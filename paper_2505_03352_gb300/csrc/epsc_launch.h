@@ -48,6 +48,7 @@ const void *pack_amax_entry();
 const void *pack_entry();
 const void *pack_finish_entry();
 const void *contract_packed_entry();
+const void *contract_packed_bulk_entry();
 
 // Seeds of Eq. 1 (factor * W), any number of regions.
 const void *seeds_entry();

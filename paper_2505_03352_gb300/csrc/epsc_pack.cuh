@@ -17,6 +17,7 @@
 #include <cuda_fp16.h>
 
 #include "epsc_common.cuh"
+#include "epsc_contract_tma.cuh"
 
 namespace epsc {
 
@@ -38,7 +39,19 @@ struct ContractPackedArgs {
   float fs[EPS_MAX_LAMBDA][3];   // scale * extra caller factors
   float *W;                      // [4][nx][ny]
   int *err;                      // error flag (debug bounds checks)
+  int nstage;                    // bulk-copy ring depth (contract_packed_bulk_kernel)
 };
+
+// Bulk-copy form of the packed contraction: PK_BY columns per chunk, one
+// thread per (column, component) of a chunk.  Wide chunks make each bulk
+// copy one long contiguous run (6 KB per component at nk = 11): measured at
+// the 3000 x 3000, eight-wavelength BF16 call, 128 columns stream the packed
+// planes in 0.90 ms where 64 or 32 take 1.28 or 2.26 ms (a fixed cost per
+// ring item, whatever the ring depth) and 256 columns at one block per SM
+// 1.26 ms.
+constexpr int PK_BY = 128;
+constexpr int PK_THREADS = 3 * PK_BY;
+constexpr int PK_MAX_STAGE = 8;
 
 // The kernels below are compiled in one translation unit only.
 #ifdef EPSC_PACK_KERNELS
@@ -169,6 +182,138 @@ __global__ void __launch_bounds__(NTHREADS) contract_packed_kernel(const __grid_
     a.W[1 * ncol + col] = wy;
     a.W[2 * ncol + col] = wzi;
     a.W[3 * ncol + col] = wzf;
+  }
+}
+
+// Untiled bulk copy of `bytes` contiguous bytes global -> shared, completing
+// on mbarrier `bar` (both addresses 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Contraction over packed fields through untiled bulk copies.  The packed
+// planes of a component are 4 np bytes per column, contiguous, so the
+// component's part of a chunk of PK_BY columns is one contiguous run: an
+// item (chunk, wavelength) is six copies (E_F and E_A, three components)
+// into one stage of an nstage-deep shared-memory ring.  Thread 0 keeps
+// nstage - 1 items in flight ahead of the consumers; every thread waits on
+// the stage's barrier itself (bounded), thread t takes column t % PK_BY and
+// component t / PK_BY of the chunk (consecutive threads read 16-byte words
+// 48 bytes apart: no bank conflicts), and one block barrier per item frees
+// the stage for the next copy.  The arithmetic per column and component is
+// contract_packed_kernel's, in the same order, so W is bitwise the same.
+// Few blocks per SM (the ring is in shared memory, not in registers) leave
+// SM slots to the stencil launched behind this grid.
+__global__ void __launch_bounds__(PK_THREADS) contract_packed_bulk_kernel(
+    const __grid_constant__ ContractPackedArgs a) {
+  extern __shared__ unsigned char pk_raw[];
+  __shared__ uint64_t full[PK_MAX_STAGE];
+  __shared__ int s_abort;
+  unsigned char *ring =
+      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(pk_raw) + 127) & ~uintptr_t(127));
+  const int tid = threadIdx.x;
+  const long ncol = (long)a.nx * a.ny;
+  const long nchunks = (ncol + PK_BY - 1) / PK_BY;
+  const int nl = a.nlambda, ns = a.nstage;
+  const unsigned colb = (unsigned)a.np * 4u;                 // bytes per column and component
+  const unsigned stage_bytes = 6u * PK_BY * colb;
+  const long my_chunks = blockIdx.x < nchunks ? (nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long total = my_chunks * nl;
+
+  griddep_launch_dependents();
+  if (tid == 0) {
+    for (int s = 0; s < ns; ++s) mbar_init(&full[s], 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+
+  auto issue = [&](long j) {
+    const int s = (int)(j % ns);
+    const long chunk = blockIdx.x + (j / nl) * gridDim.x;
+    const int l = (int)(j % nl);
+    const long col0 = chunk * PK_BY;
+    const unsigned n = (unsigned)min((long)PK_BY, ncol - col0);
+    unsigned char *dst = ring + (size_t)s * stage_bytes;
+    mbar_arrive_expect_tx(&full[s], 6u * n * colb);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const unsigned char *base = (f == 0 ? a.EF[l] : a.EA[l]) + 16;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        bulk_load(dst + (f * 3 + c) * PK_BY * colb, base + ((size_t)c * ncol + col0) * colb,
+                  n * colb, &full[s]);
+    }
+  };
+  if (tid == 0)
+    for (long j = 0; j < min((long)ns, total); ++j) issue(j);
+
+  const int c = tid / PK_BY, col = tid - c * PK_BY;
+  const int nq = a.np >> 2;
+  float acc_in = 0.f, acc_face = 0.f;
+  long consumed = 0;
+  for (long i = 0; i < total; ++i) {
+    const int s = (int)(i % ns);
+    const bool ok = mbar_wait_bounded(&full[s], (unsigned)((i / ns) & 1));
+    if (!ok) s_abort = 1;
+    const int l = (int)(i % nl);
+    if (ok) {
+      const uint4 *pf = reinterpret_cast<const uint4 *>(ring + (size_t)s * stage_bytes +
+                                                        (c * PK_BY + col) * colb);
+      const uint4 *pa = reinterpret_cast<const uint4 *>(ring + (size_t)s * stage_bytes +
+                                                        ((3 + c) * PK_BY + col) * colb);
+      float s_in = 0.f, s_face = 0.f;
+      for (int q = 0; q < nq; ++q) {
+        const uint4 f = pf[q];
+        const uint4 e = pa[q];
+        const unsigned fb[4] = {f.x, f.y, f.z, f.w};
+        const unsigned eb[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int kk = 4 * q + t;   // packed plane kk is plane k0 + kk
+          const float2 x = unpack2(fb[t], a.type);
+          const float2 y = unpack2(eb[t], a.type);
+          const float re = fmaf(x.x, y.x, -x.y * y.y);
+          const bool in = c < 2 ? (kk >= 1 && kk <= a.nk) : (kk >= 1 && kk <= a.nk - 1);
+          const bool face = c == 2 && (kk == 0 || kk == a.nk);
+          s_in += in ? re : 0.f;
+          s_face += face ? re : 0.f;
+        }
+      }
+      const float sc = __ldg(reinterpret_cast<const float *>(a.EF[l]) + c) *
+                       __ldg(reinterpret_cast<const float *>(a.EA[l]) + c) * a.fs[l][c];
+      // a rounded product, then a rounded sum, per wavelength
+      acc_in = __fadd_rn(acc_in, __fmul_rn(s_in, sc));
+      if (c == 2) acc_face = __fadd_rn(acc_face, __fmul_rn(s_face, sc));
+      if (l == nl - 1) {
+        const long gcol = (blockIdx.x + (i / nl) * gridDim.x) * PK_BY + col;
+        if (gcol < ncol) {
+          a.W[(size_t)c * ncol + gcol] = acc_in;
+          if (c == 2) a.W[3 * (size_t)ncol + gcol] = acc_face;
+        }
+        acc_in = acc_face = 0.f;
+      }
+    }
+    __syncthreads();   // stage s fully read (and every thread's timeout flag visible)
+    if (s_abort) break;
+    consumed = i + 1;
+    if (tid == 0 && i + ns < total) issue(i + ns);
+  }
+
+  if (s_abort) {
+    // record the timeout, then let every copy this block issued land before
+    // its shared memory is released (each wait bounded again)
+    if (tid == 0) {
+      atomicOr(a.err, ERRFLAG_TIMEOUT);
+      const long issued = min(total, consumed + ns);
+      for (long j = consumed; j < issued; ++j)
+        mbar_wait_bounded(&full[j % ns], (unsigned)((j / ns) & 1));
+    }
+    __syncthreads();
   }
 }
 

@@ -9,5 +9,6 @@ const void *pack_amax_entry() { return (const void *)&pack_amax_kernel; }
 const void *pack_entry() { return (const void *)&pack_kernel; }
 const void *pack_finish_entry() { return (const void *)&pack_finish_kernel; }
 const void *contract_packed_entry() { return (const void *)&contract_packed_kernel; }
+const void *contract_packed_bulk_entry() { return (const void *)&contract_packed_bulk_kernel; }
 
 }  // namespace epsc
