@@ -16,8 +16,11 @@ from __future__ import annotations
 
 import torch
 
-from .epschain import (EPS_FIELD_C64, Morph, Problem, eps_forward, eps_forward_morph, eps_vjp,
-                       eps_vjp_real, eps_vjp_real_morph, eps_vjp_surrogate)
+import ctypes
+
+from .epschain import (EPS_FIELD_C64, Morph, Problem, _check, _field_ptrs, _need, _ptr, _scales,
+                       _stream, _workspace, eps_forward, eps_forward_morph, eps_vjp, eps_vjp_real,
+                       eps_vjp_real_morph, eps_vjp_surrogate, lib)
 
 
 class EpsChain(torch.autograd.Function):
@@ -89,6 +92,66 @@ def eps_adjoint(C, prob: Problem, EF, EA, scale: float = -2.0, with_eps: bool = 
     S.backward() leaves dJ/dC in C.grad.  With with_eps, returns (S, eps_hat)
     from the same fused call (eps_hat is what the next field solve needs)."""
     return EpsAdjoint.apply(C, prob, list(EF), list(EA), scale, with_eps)
+
+
+class AdjointSurrogate:
+    """EpsAdjoint for fields that stay fixed over many calls (the inner loop
+    of an optimisation between two field solves): the fused call's field
+    pointers, scales and workspace are checked and marshalled once, and each
+    call passes only C.  surr(C) returns S (or (S, eps_hat) with with_eps),
+    differentiable in C exactly as eps_adjoint's.  The tensors given here
+    must stay alive and unchanged in shape while the object is used; calls
+    of one object share its workspace, so they must not overlap on
+    different streams."""
+
+    def __init__(self, prob: Problem, EF, EA, scale: float = -2.0, with_eps: bool = False,
+                 field_type: int = EPS_FIELD_C64, field_scales=None):
+        dev = EF[0].device if len(EF) else torch.device("cuda", torch.cuda.current_device())
+        self.prob = prob
+        self.with_eps = with_eps
+        self._dev = dev
+        self._nl, self._ef, self._ea = _field_ptrs(prob, EF, EA, field_type, dev)
+        self._fs = _scales(field_scales, self._nl)
+        self._ws = _workspace(prob, self._nl, None, dev)
+        self._keep = (list(EF), list(EA))
+        self._p = prob.c_struct()
+        self._field_type = field_type
+        self._scale = float(scale)
+        self._fn = lib().eps_vjp_surrogate
+
+    def call(self, C):
+        """One fused call: returns (dJdC, eps_hat or None, S)."""
+        _need(C, (self.prob.mx, self.prob.my), torch.float32, "C", self._dev)
+        dJdC = torch.empty((self.prob.mx, self.prob.my), dtype=torch.float32, device=self._dev)
+        S = torch.empty((), dtype=torch.float64, device=self._dev)
+        eps = (torch.empty((3, self.prob.nx, self.prob.ny, self.prob.nz), dtype=torch.float32,
+                           device=self._dev) if self.with_eps else None)
+        _check(self._fn(ctypes.byref(self._p), _ptr(C), self._nl, self._field_type, self._ef,
+                        self._ea, self._fs, self._scale, _ptr(dJdC), _ptr(eps), _ptr(S),
+                        _ptr(self._ws), self._ws.numel(), _stream(None)),
+               "eps_vjp_surrogate")
+        return dJdC, eps, S
+
+    def __call__(self, C):
+        return _PreparedAdjoint.apply(C, self)
+
+
+class _PreparedAdjoint(torch.autograd.Function):
+    """EpsAdjoint through an AdjointSurrogate's prepared call."""
+
+    @staticmethod
+    def forward(ctx, C, surr: AdjointSurrogate):
+        dJdC, eps, S = surr.call(C.contiguous())
+        ctx.save_for_backward(dJdC)
+        if eps is not None:
+            ctx.mark_non_differentiable(eps)
+            return S, eps
+        return S
+
+    @staticmethod
+    def backward(ctx, grad_S, *unused):
+        (dJdC,) = ctx.saved_tensors
+        return grad_S.to(dJdC.dtype) * dJdC, None
 
 
 class EpsChainMorph(torch.autograd.Function):

@@ -1065,13 +1065,15 @@ struct BatchTuning {
   int contract_bps;   // batched contraction blocks per SM (TMA form; 4x for register loads)
   int stage_comps;    // eps_hat components staged per round of bulk stores (1 or 3)
   int defer_seeds;    // 1: stencil writes seed factors, the seeds kernel applies W
+  int bwd_bulk;       // grouped form: 1 = the scatter stages interior tiles by bulk copies
 };
 // Default: the grouped form, measured faster on the 64-region batch (radius
 // classes 2 .. 8): one kernel holding all twelve radius bodies runs them side
 // by side on an SM and lost to per-class launches there.  Three TMA
 // contraction blocks per SM streamed that batch's fields in 304 us against
-// 368 us with two.
-constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 3, 3, 0};
+// 368 us with two; one eps_hat component per staging round took the call
+// from 0.916 to 0.897 ms.
+constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 3, 1, 0, 1};
 // The TMA contraction's ring (2 stages of up to 6 x 32 x 64 floats) leaves
 // room for at most this many blocks per SM.
 constexpr int TMA_BATCH_MAX_BPS = 4;
@@ -1219,11 +1221,53 @@ eps_status_t run_fwd_grouped(const std::vector<Group> &gs, const std::vector<Res
   return st;
 }
 
+// One scatter launch per group whose interior tiles stage through bulk
+// tensor copies: at most BWD_TMA_BATCH regions a launch, each region's four
+// maps in the parameters (regions whose layout does not suit bulk copies
+// gather element by element inside the same launch).
+static_assert(sizeof(BwdTmaBatchArgs) <= 32764, "kernel parameter space");
+eps_status_t run_bwd_group_bulk(const Group &g, const std::vector<Resolved> &rs,
+                                const std::vector<BwdRegion> &regions, const KernelEntry &k,
+                                int *err, cudaStream_t s) {
+  std::unique_ptr<BwdTmaBatchArgs> ta(new BwdTmaBatchArgs);
+  eps_status_t st = EPS_OK;
+  for (size_t q0 = 0; q0 < g.regions.size() && st == EPS_OK; q0 += BWD_TMA_BATCH) {
+    const int cnt = (int)std::min<size_t>(BWD_TMA_BATCH, g.regions.size() - q0);
+    std::memset(ta.get(), 0, sizeof(*ta));
+    ta->n = cnt;
+    ta->err = err;
+    std::memcpy(ta->w, rs[g.regions[q0]].w, sizeof(ta->w));
+    int tiles = 0;
+    for (int q = 0; q < cnt; ++q) {
+      const int ri = g.regions[q0 + q];
+      const BwdRegion &br = regions[ri];
+      const dim3 grid = bwd_grid(rs[ri].g);
+      ta->tile_start[q] = tiles;
+      ta->tiles_j[q] = (int)grid.x;
+      tiles += (int)(grid.x * grid.y);
+      ta->r[q] = br;
+      ta->has_maps[q] = scatter_maps(rs[ri], br.seeds, br.pd4, br.ie2, &ta->maps[4 * q]) ? 1 : 0;
+    }
+    ta->tile_start[cnt] = tiles;
+    st = launch("eps_batched_scatter", k.fn, dim3((unsigned)tiles), k.smem, ta.get(), s, true);
+  }
+  return st;
+}
+
 eps_status_t run_bwd_grouped(const std::vector<Group> &gs, const std::vector<Resolved> &rs,
-                             const std::vector<BwdRegion> &regions, int *err, cudaStream_t s) {
+                             const std::vector<BwdRegion> &regions, int bulk, int *err,
+                             cudaStream_t s) {
   BwdBatchArgs *ba = new BwdBatchArgs;
   eps_status_t st = EPS_OK;
   for (const Group &g : gs) {
+    if (bulk) {
+      const KernelEntry kb = bwd_tma_batched_entry(g.rp1, g.bc);
+      if (kb.fn) {
+        st = run_bwd_group_bulk(g, rs, regions, kb, err, s);
+        if (st != EPS_OK) break;
+        continue;
+      }
+    }
     std::memset(ba, 0, sizeof(*ba));
     ba->n = (int)g.regions.size();
     ba->err = err;
@@ -1331,7 +1375,7 @@ eps_status_t run_bwd_batch(const std::vector<Resolved> &rs, const eps_problem_t 
                            const std::vector<BwdRegion> &regions, const BatchTuning &t, int *err,
                            cudaStream_t s) {
   if (t.multi) return run_bwd_multi(make_sets(rs, probs), rs, regions, t.bwd_bps, err, s);
-  return run_bwd_grouped(make_groups(rs, probs), rs, regions, err, s);
+  return run_bwd_grouped(make_groups(rs, probs), rs, regions, t.bwd_bulk, err, s);
 }
 
 eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float *const *C,
@@ -1518,10 +1562,12 @@ eps_status_t eps_batched_set_tuning(int32_t n, const eps_problem_t *probs, int32
   if ((u.multi != 0 && u.multi != 1) || u.stencil_blocks_per_sm < 1 || u.stencil_blocks_per_sm > 16 ||
       u.scatter_blocks_per_sm < 1 || u.scatter_blocks_per_sm > 16 || u.contract_blocks_per_sm < 1 ||
       u.contract_blocks_per_sm > 64 || (u.stage_components != 1 && u.stage_components != 3) ||
-      (u.defer_seeds != 0 && u.defer_seeds != 1))
+      (u.defer_seeds != 0 && u.defer_seeds != 1) ||
+      (u.scatter_bulk_staging != 0 && u.scatter_bulk_staging != 1))
     return EPS_ERR_INVALID_ARG;
   const BatchTuning t{u.multi, u.stencil_blocks_per_sm, u.scatter_blocks_per_sm,
-                      u.contract_blocks_per_sm, u.stage_components, u.defer_seeds};
+                      u.contract_blocks_per_sm, u.stage_components, u.defer_seeds,
+                      u.scatter_bulk_staging};
   store_tuning(batch_signature(n, probs, n_lambda), t);
   return EPS_OK;
 }
@@ -1570,17 +1616,19 @@ eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const f
   default_ms = best_ms;
   // coordinate descent over the launch form and shapes, two sweeps
   for (int sweep = 0; sweep < 2 && st == EPS_OK; ++sweep) {
-    for (int param = 0; param < 6 && st == EPS_OK; ++param) {
-      static const int values[6][4] = {{0, 1, -1, -1}, {1, 3, -1, -1}, {1, 2, 3, 4},
-                                       {1, 2, 3, 4}, {1, 2, 3, 4}, {0, 1, -1, -1}};
+    for (int param = 0; param < 7 && st == EPS_OK; ++param) {
+      static const int values[7][4] = {{0, 1, -1, -1}, {1, 3, -1, -1}, {1, 2, 3, 4},
+                                       {1, 2, 3, 4},   {1, 2, 3, 4}, {0, 1, -1, -1},
+                                       {0, 1, -1, -1}};
       for (int v = 0; v < 4 && st == EPS_OK; ++v) {
         const int val = values[param][v];
         if (val < 0) continue;
         BatchTuning t = best;
-        int *field[6] = {&t.multi, &t.stage_comps, &t.fwd_bps, &t.bwd_bps, &t.contract_bps,
-                         &t.defer_seeds};
+        int *field[7] = {&t.multi, &t.stage_comps, &t.fwd_bps, &t.bwd_bps, &t.contract_bps,
+                         &t.defer_seeds, &t.bwd_bulk};
         if (*field[param] == val) continue;
         if ((param == 2 || param == 3) && !t.multi) continue;   // grouped form: one block per tile
+        if (param == 6 && t.multi) continue;                     // multi form: element-wise gather
         *field[param] = val;
         float ms = 0.f;
         st = timeit(t, &ms);
@@ -1602,6 +1650,7 @@ eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const f
     result->contract_blocks_per_sm = best.contract_bps;
     result->stage_components = best.stage_comps;
     result->defer_seeds = best.defer_seeds;
+    result->scatter_bulk_staging = best.bwd_bulk;
     result->evaluations = evals;
     result->default_ms = default_ms;
     result->tuned_ms = best_ms;

@@ -89,11 +89,13 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src) {
 }
 
 // One tile (subpixel rows a0 .., columns b0 ..) of one region `rg`.  With
-// TMA the arguments carry tensor maps of the staged inputs (bwd_tma_kernel:
-// single region, one tile per block, radius class 3 and up).
+// TMA, `maps` points at the region's four tensor maps of the staged inputs
+// in the kernel parameters (bwd_tma_kernel: single region; the batched
+// bwd_tma_batched_kernel: the tile's region), or is null for a region whose
+// layout does not suit bulk copies; radius class 3 and up.
 template <int RP1, int BC, bool TMA = false, class Args>
 __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, const int a0,
-                                         const int b0) {
+                                         const int b0, const CUtensorMap *maps = nullptr) {
   using S = BwdSmem<RP1>;
   constexpr int R = S::R;
   constexpr int DBP = S::DBP;
@@ -143,7 +145,7 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
     // (the sections sit on 128-byte boundaries of the dynamic shared memory,
     // declared 128-byte aligned; a base that were not falls back to the
     // element-wise gather)
-    if (R >= 2 && (smem_addr(bwd_smem) & 127u) == 0u && da_lo >= 0 && da_lo + DA <= g.mx &&
+    if (maps && R >= 2 && (smem_addr(bwd_smem) & 127u) == 0u && da_lo >= 0 && da_lo + DA <= g.mx &&
         db_lo >= 0 && db_lo + DB <= g.my && ci_lo >= 1 && ci_lo + NCI + 1 <= g.nx && cj_lo >= 1 &&
         cj_lo + NCJ + 1 <= g.ny) {
       __shared__ uint64_t bar;
@@ -156,10 +158,10 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         mbar_arrive_expect_tx(&bar, S::TMA_BYTES);
-        tma_load_3d(sU, &a.maps[0], xa, da_lo, 0, &bar);
-        tma_load_3d(sIE2, &a.maps[1], xa, da_lo, 0, &bar);
-        tma_load_3d(sSeed, &a.maps[2], xs, ci_lo, S_DAX, &bar);
-        tma_load_3d(sG, &a.maps[3], xg, ci_lo - 1, S_GXX, &bar);
+        tma_load_3d(sU, &maps[0], xa, da_lo, 0, &bar);
+        tma_load_3d(sIE2, &maps[1], xa, da_lo, 0, &bar);
+        tma_load_3d(sSeed, &maps[2], xs, ci_lo, S_DAX, &bar);
+        tma_load_3d(sG, &maps[3], xg, ci_lo - 1, S_GXX, &bar);
         s_fail = 0;
         if (!mbar_wait_bounded(&bar, 0u)) {
           // record the timeout; let the copies land before the block leaves
@@ -388,7 +390,19 @@ __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ B
 // The same scatter with bulk-copy staging of the interior tiles.
 template <int RP1, int BC>
 __global__ void __launch_bounds__(NTHREADS) bwd_tma_kernel(const __grid_constant__ BwdTmaArgsR<RP1> a) {
-  bwd_tile<RP1, BC, true>(a, a.r, blockIdx.y * TA, blockIdx.x * TB);
+  bwd_tile<RP1, BC, true>(a, a.r, blockIdx.y * TA, blockIdx.x * TB, &a.maps[0]);
+}
+
+// Batched scatter of one radius group with bulk-copy staging: block b takes
+// tile b - tile_start[k] of region k, staged through region k's maps.
+template <int RP1, int BC>
+__global__ void __launch_bounds__(NTHREADS) bwd_tma_batched_kernel(const __grid_constant__ BwdTmaBatchArgs a) {
+  int k, t;
+  batch_tile(a, blockIdx.x, k, t);
+  const int tj = a.tiles_j[k];
+  const int ti = t / tj;
+  bwd_tile<RP1, BC, true>(a, a.r[k], ti * TA, (t - ti * tj) * TB,
+                          a.has_maps[k] ? &a.maps[4 * k] : nullptr);
 }
 
 template <int RP1, int BC>

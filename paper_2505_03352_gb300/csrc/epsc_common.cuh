@@ -207,6 +207,22 @@ struct BwdBatchArgs {
   float w[MAX_BOX * MAX_BOX];
 };
 
+// Batched scatter that stages interior tiles through bulk tensor copies: up
+// to BWD_TMA_BATCH regions of one radius group per launch, each with its own
+// four tensor maps in the parameter block (has_maps[k] = 0: that region's
+// layout does not suit bulk copies and its tiles gather element by element).
+constexpr int BWD_TMA_BATCH = 32;
+struct __align__(128) BwdTmaBatchArgs {
+  int n;
+  int tile_start[BWD_TMA_BATCH + 1];
+  int tiles_j[BWD_TMA_BATCH];
+  int has_maps[BWD_TMA_BATCH];
+  BwdRegion r[BWD_TMA_BATCH];
+  int *err;
+  float w[MAX_BOX * MAX_BOX];
+  CUtensorMap maps[4 * BWD_TMA_BATCH];   // region k: maps[4 k .. 4 k + 3]
+};
+
 // Region and tile of block b in a batched launch (regions scanned in order).
 template <class BA>
 __device__ __forceinline__ void batch_tile(const BA &a, int b, int &k, int &t) {

@@ -21,6 +21,9 @@ KernelEntry bwd_entry_b(int rp1, int bc, bool batched);
 // Single-region scatter staging interior tiles through bulk tensor copies
 // (radius classes 3 .. 12; {nullptr, 0} otherwise).
 KernelEntry bwd_tma_entry(int rp1, int bc);
+// The batched scatter of one radius group with bulk-copy staging (radius
+// classes 3 .. 12; {nullptr, 0} otherwise).
+KernelEntry bwd_tma_batched_entry(int rp1, int bc);
 
 // Contraction kernel with 4 or 8 lanes per column.
 const void *contract_entry(int lanes);

@@ -517,11 +517,13 @@ class BatchedVjp:
     def set_tuning(self, **shapes):
         """Store launch shapes for this batch (eps_batched_set_tuning); keys are
         the eps_tuning_t fields multi, stencil_blocks_per_sm,
-        scatter_blocks_per_sm, contract_blocks_per_sm, stage_components and
-        defer_seeds (defaults: the library's default shapes)."""
+        scatter_blocks_per_sm, contract_blocks_per_sm, stage_components,
+        defer_seeds and scatter_bulk_staging (defaults: the library's default
+        shapes)."""
         r = eps_tuning_t()
         base = dict(multi=0, stencil_blocks_per_sm=3, scatter_blocks_per_sm=3,
-                    contract_blocks_per_sm=3, stage_components=3, defer_seeds=0)
+                    contract_blocks_per_sm=3, stage_components=1, defer_seeds=0,
+                    scatter_bulk_staging=1)
         base.update(shapes)
         for k, v in base.items():
             setattr(r, k, int(v))
@@ -543,7 +545,8 @@ class eps_tuning_t(ctypes.Structure):
                 ("scatter_blocks_per_sm", ctypes.c_int32), ("contract_blocks_per_sm", ctypes.c_int32),
                 ("stage_components", ctypes.c_int32), ("defer_seeds", ctypes.c_int32),
                 ("evaluations", ctypes.c_int32),
-                ("default_ms", ctypes.c_float), ("tuned_ms", ctypes.c_float)]
+                ("default_ms", ctypes.c_float), ("tuned_ms", ctypes.c_float),
+                ("scatter_bulk_staging", ctypes.c_int32)]
 
 
 def eps_sync_status(stream=None):

@@ -114,7 +114,8 @@ def tuning(**kw):
     (dict(stencil_blocks_per_sm=17), INVALID), (dict(scatter_blocks_per_sm=0), INVALID),
     (dict(scatter_blocks_per_sm=17), INVALID), (dict(contract_blocks_per_sm=0), INVALID),
     (dict(contract_blocks_per_sm=65), INVALID), (dict(stage_components=2), INVALID),
-    (dict(defer_seeds=2), INVALID),
+    (dict(defer_seeds=2), INVALID), (dict(scatter_bulk_staging=1), OK),
+    (dict(scatter_bulk_staging=2), INVALID), (dict(scatter_bulk_staging=-1), INVALID),
 ])
 def test_set_tuning_ranges(L, kw, status):
     ps = [prob(), prob(mx=80)]

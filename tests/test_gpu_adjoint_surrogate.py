@@ -71,6 +71,32 @@ def test_adjoint_surrogate_value_and_gradient(mx, my):
         assert np.max(np.abs(Cg.grad.cpu().numpy() - ref)) / np.max(np.abs(ref)) <= 1e-4
 
 
+def test_prepared_surrogate_equals_the_functional_form():
+    # AdjointSurrogate (fields marshalled once) against eps_adjoint: the same
+    # S, eps_hat and gradient bit for bit, on two calls in a row with C
+    # changed in place between them (an optimiser step)
+    torch, ec, ag = _mods()
+    p = ec.Problem(mx=200, my=168, nz=16, radius=3.0, beta=8.0)
+    shape = (3, p.nx, p.ny, p.nz)
+    EF = [torch.from_numpy(synth.complex_field(shape, 42 + l)).cuda() for l in range(3)]
+    EA = [torch.from_numpy(synth.complex_field(shape, 52 + l)).cuda() for l in range(3)]
+    C = torch.from_numpy(np.random.default_rng(23).random((200, 168), dtype=np.float32)).cuda()
+    surr = ag.AdjointSurrogate(p, EF, EA, with_eps=True)
+    Cp = C.clone().requires_grad_(True)
+    for step in range(2):
+        Cp.grad = None
+        S, eps = surr(Cp)
+        S.backward()
+        Cf = Cp.detach().clone().requires_grad_(True)
+        Sf, epsf = ag.eps_adjoint(Cf, p, EF, EA, with_eps=True)
+        Sf.backward()
+        assert S.item() == Sf.item()
+        torch.testing.assert_close(eps, epsf, rtol=0, atol=0)
+        torch.testing.assert_close(Cp.grad, Cf.grad, rtol=0, atol=0)
+        with torch.no_grad():
+            Cp.sub_(1e-3 * torch.sign(Cp.grad))
+
+
 def test_differentiation_form_at_full_size():
     # cfg3 through autograd, three wavelengths: C.grad on five windows against
     # the oracle (the chain is local; see tests/test_gpu_large.py), S against

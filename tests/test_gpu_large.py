@@ -110,7 +110,7 @@ def test_cfg5_eight_wavelengths_at_full_size():
     # 3000 x 3000 controls, 1500 x 1500 x 32, eight wavelengths (27.6 GB of
     # complex64 fields on the device), in the bench's launch configuration;
     # the FP32 path within the oracle tolerance, BF16 and FP16 fields within
-    # their quantisation error (the errors the bench states)
+    # about 1.5 times their measured quantisation error
     import torch
 
     import paper_2505_03352_gb300 as ec
@@ -127,12 +127,17 @@ def test_cfg5_eight_wavelengths_at_full_size():
     worst_e, worst_g = window_check_device(w, C, EF, EA, e, g, windows)
     assert worst_e <= EPS_TOL, worst_e
     assert worst_g <= GRAD_TOL, worst_g
-    for ft, bound in ((ec.EPS_FIELD_BF16X2_SCALED, 2e-2), (ec.EPS_FIELD_F16X2_SCALED, 2e-3)):
+    print(f"cfg5 FP32: eps_hat {worst_e:.3e}, dJ/dC {worst_g:.3e}")
+    # quantisation error of the packed formats on these windows, measured on
+    # a GB300: BF16 6.29e-3, FP16 4.10e-4 of the largest value; the gates sit
+    # about 1.5 times above (the inputs and the kernels are deterministic)
+    for ft, bound in ((ec.EPS_FIELD_BF16X2_SCALED, 9.5e-3), (ec.EPS_FIELD_F16X2_SCALED, 6.2e-4)):
         PF = [ec.eps_field_pack(p, ft, x) for x in EF]
         PA = [ec.eps_field_pack(p, ft, x) for x in EA]
         gq = ec.eps_vjp(p, Cd, PF, PA, field_type=ft)
         ec.eps_sync_status()
         _, worst_q = window_check_device(w, C, EF, EA, None, gq.cpu().numpy(), windows[:3])
+        print(f"cfg5 field type {ft}: dJ/dC {worst_q:.3e}")
         assert worst_q <= bound, (ft, worst_q)
         del PF, PA
     del EF, EA
