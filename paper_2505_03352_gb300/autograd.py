@@ -72,6 +72,9 @@ class EpsAdjoint(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, C, prob: Problem, EF, EA, scale: float = -2.0, with_eps: bool = False):
+        # eps_hat is not differentiable: without this, autograd would fill a
+        # zero gradient of eps_hat's size (hundreds of MB) for every backward
+        ctx.set_materialize_grads(False)
         C = C.contiguous()
         if with_eps:
             dJdC, eps, S = eps_vjp_surrogate(prob, C, EF, EA, scale=scale, eps_out=True)
@@ -84,6 +87,8 @@ class EpsAdjoint(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_S, *unused):
         (dJdC,) = ctx.saved_tensors
+        if grad_S is None:
+            return None, None, None, None, None, None
         return grad_S.to(dJdC.dtype) * dJdC, None, None, None, None, None
 
 
@@ -141,6 +146,7 @@ class _PreparedAdjoint(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, C, surr: AdjointSurrogate):
+        ctx.set_materialize_grads(False)   # no zero gradient of eps_hat (see EpsAdjoint)
         dJdC, eps, S = surr.call(C.contiguous())
         ctx.save_for_backward(dJdC)
         if eps is not None:
@@ -151,6 +157,8 @@ class _PreparedAdjoint(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_S, *unused):
         (dJdC,) = ctx.saved_tensors
+        if grad_S is None:
+            return None, None
         return grad_S.to(dJdC.dtype) * dJdC, None
 
 
