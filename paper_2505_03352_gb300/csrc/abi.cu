@@ -227,6 +227,8 @@ dim3 bwd_grid(const Geometry &g) { return dim3((g.my + TB - 1) / TB, (g.mx + TA 
 // Dynamic shared memory of a forward launch: the stencil buffers, grown to
 // stage all of the tile's eps_hat components (up to 3) for one round of bulk
 // stores when that fits the budget.
+// (ncomp = 0: eps_hat leaves by direct coalesced stores; only the stencil
+// buffers are needed)
 size_t fwd_smem(const KernelEntry &k, const Geometry &g, int ncomp, int *stage_floats) {
   const size_t comp_bytes = sizeof(float) * TI * TJ * (size_t)g.nz;
   size_t want = std::max(k.smem, std::min<size_t>(ncomp, 3) * comp_bytes);
@@ -512,7 +514,7 @@ eps_status_t run_seeds(const SeedsArgs &sa, cudaStream_t s) {
 // (Measured alternatives that lost: a persistent stencil of 2 or 3 blocks
 // per SM finishing its seeds after its last tile, and 1-component staging.)
 struct StencilForm {
-  int defer, stage_comps;
+  int defer, stage_comps;   // stage_comps 0: eps_hat by direct coalesced stores
 };
 constexpr int ONE_WAVE_TILES_PER_SM = 3;
 constexpr StencilForm FORM_ONE_WAVE{0, 3};
@@ -520,7 +522,9 @@ constexpr StencilForm FORM_ONE_WAVE{0, 3};
 // memory at nz = 32 instead of 98 KB, so four stencil blocks fit on an SM
 // (or some beside the field contraction).  Measured: the 2000 x 2000,
 // three-wavelength call 526 -> 519 us, the 3000 x 3000 eight-wavelength
-// call 2.41 -> 2.39 ms (FP32) and 1.44 -> 1.23 ms (BF16).
+// call 2.41 -> 2.39 ms (FP32) and 1.44 -> 1.23 ms (BF16).  Direct stores
+// (stage_comps 0) measured no better in the fused calls (BF16 1.25 ms,
+// 600 x 600 call 47.6 against 44.3 us), so the fused forms keep staging.
 constexpr StencilForm FORM_MULTI_WAVE{1, 1};
 
 eps_status_t stencil_form(const Geometry &g, StencilForm *f, long *blocks) {
@@ -691,10 +695,16 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps, 
   fa.r.eps = eps;
   fa.r.offdiag = od ? offdiag : nullptr;
   const KernelEntry k = fwd_entry(r.rp1, r.g.bc);
-  // one eps_hat component staged per round (the stencil's own buffers are
-  // the larger part then): more resident blocks; the 2000 x 2000 forward
-  // went from 197 to 150 us against three components per round
-  const size_t smem = fwd_smem(k, r.g, od ? 5 : 1, &fa.r.stage_floats);
+  // More than one wave of tiles: eps_hat leaves by warp-cooperative direct
+  // stores (no staging, only the stencil's 31 KB of shared memory); within
+  // one wave, one component staged per round.  Measured on a GB300: the
+  // 2000 x 2000 forward 197 us (three components staged) -> 154 us (one) ->
+  // 136 us (direct); the 600 x 600 forward 19.2 us staged, 21.2 us direct.
+  int nsm = 0;
+  if ((st = sm_count(&nsm)) != EPS_OK) return st;
+  const bool direct = fwd_ntiles(r.g) > (long)ONE_WAVE_TILES_PER_SM * nsm && (r.g.nz & 3) == 0;
+  fa.r.direct_eps = direct ? 1 : 0;
+  const size_t smem = fwd_smem(k, r.g, direct ? 0 : (od ? 5 : 1), &fa.r.stage_floats);
   return launch("eps_forward", k.fn, dim3((unsigned)fwd_ntiles(r.g)), smem, &fa, (cudaStream_t)stream);
 }
 
@@ -816,6 +826,7 @@ eps_status_t vjp_fused(const eps_problem_t *prob, const float *C, int32_t n_lamb
     fa.r.epsc = form.defer ? epsc : nullptr;
   }
   const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
+  fa.r.direct_eps = (eps_out && form.stage_comps == 0) ? 1 : 0;
   const size_t smem =
       fwd_smem(kf, r.g, eps_out ? std::min(3, form.stage_comps) : 0, &fa.r.stage_floats);
   st = launch(eps_out ? "eps_fwd_vjp_stencil" : "eps_vjp_stencil", kf.fn, dim3((unsigned)blocks),

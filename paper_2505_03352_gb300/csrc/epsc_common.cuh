@@ -84,6 +84,8 @@ struct FwdRegion {
   int defer_seeds;               // VJP: 0 = wait for the contraction and write the seeds,
                                  //      1 = write seed factors (the seeds kernel applies W)
   int stage_floats;              // shared floats available for eps_hat staging
+  int direct_eps;                // 1: eps_hat leaves by warp-cooperative coalesced stores
+                                 //    (no staging; nz a multiple of 4)
   const float *C;
   float *eps;
   float *offdiag;

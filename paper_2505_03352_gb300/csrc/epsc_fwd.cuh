@@ -277,7 +277,41 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
     const size_t cplane = (size_t)g.nx * g.ny * g.nz;
     const int comp_floats = TI * TJ * g.nz;
     const int per_round = rg.stage_floats / comp_floats;
-    if ((g.nz & 3) == 0 && per_round >= 1) {
+    if ((g.nz & 3) == 0 && rg.direct_eps) {
+      // Warp-cooperative stores, no shared memory: warp cr (one tile row,
+      // lane = column) writes its row's contiguous run of nvj * nz floats per
+      // component, 16 coalesced bytes a lane per store; each lane takes the
+      // owning column's values from that column's lane by shuffle.  The
+      // values are those the staging below writes.
+      const int nz4 = g.nz >> 2;
+      if (cr < nvi) {   // uniform over the warp
+        const size_t roff = ((size_t)(i0 + cr) * g.ny + j0) * g.nz;
+        const int nf4 = nvj * nz4;
+        for (int comp = c_first; comp <= c_last; ++comp) {
+          const float vm = comp == 0 ? ex : comp == 1 ? ey : comp == 2 ? ezi : comp == 3 ? odx
+                           : comp == 4 ? ody : comp == 5 ? ezx3 : ezy3;
+          const float outv = comp < 3 ? g.eps_clad : 0.f;
+          float *base = comp < 3 ? rg.eps + comp * cplane : rg.offdiag + (comp - 3) * cplane;
+          if (!EPSC_IN_BOUNDS((comp < 3 ? comp : comp - 3) * cplane + roff, (size_t)nf4 * 4,
+                              (comp < 3 ? 3 : (rg.normals3d ? 4 : 2)) * cplane, a.err))
+            continue;
+          float4 *dst = reinterpret_cast<float4 *>(base + roff);
+          for (int f0 = 0; f0 < nf4; f0 += 32) {
+            const int f = f0 + cc;
+            const int jj = min(f / nz4, 31);
+            const float v = __shfl_sync(0xffffffffu, vm, jj);
+            const float vf = __shfl_sync(0xffffffffu, ezf3, jj);
+            if (f < nf4) {
+              const int k = 4 * (f - (f / nz4) * nz4);
+              float t[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) t[q] = plane_value(comp, k + q, g.k0, g.nk, v, v, vf, outv);
+              __stcs(dst + f, make_float4(t[0], t[1], t[2], t[3]));
+            }
+          }
+        }
+      }
+    } else if ((g.nz & 3) == 0 && per_round >= 1) {
       float *sbuf = smem;   // the stencil buffers are dead from here on
       const int nz4 = g.nz >> 2;
       __syncthreads();
