@@ -790,6 +790,15 @@ def run_variants(torch, ec, synth, dev, flush_l2,
         with torch.cuda.graph(graph):
             bv()
         ms_b = _timed(graph.replay, flush_l2, 20, torch)
+        # the other scatter tile shape, forced (the tuner's pick stays cached
+        # for the graph above)
+        alt_cols = 64 if tuning.get("scatter_tile_cols", 32) == 32 else 32
+        shapes = {k: tuning[k] for k in ("multi", "stencil_blocks_per_sm", "scatter_blocks_per_sm",
+                                         "contract_blocks_per_sm", "stage_components",
+                                         "defer_seeds", "scatter_bulk_staging")}
+        bv.set_tuning(**shapes, scatter_tile_cols=alt_cols)
+        ms_alt = _timed(bv, flush_l2, 20, torch)
+        bv.set_tuning(**shapes, scatter_tile_cols=tuning.get("scatter_tile_cols", 32))
         singles = [ec.PreparedVjp(p, C, ef, ea, G, eps_out=E)
                    for p, C, ef, ea, G, E in zip(probs, Cs, EFs, EAs, bv.dJdC, bv.eps)]
 
@@ -807,6 +816,8 @@ def run_variants(torch, ec, synth, dev, flush_l2,
                 "value": vox / (ms_s * 1e-3), "ms_per_call": round(ms_s, 4)},
             "speedup_vs_per_region": round(ms_s / ms_b, 3),
             "default_shapes_ms_per_call": round(ms_default, 4), "autotuned": tuning,
+            "other_scatter_tile": {"cols": alt_cols, "ms_per_call": round(ms_alt, 4),
+                                   "note": "same shapes, the other scatter tile width, no graph"},
             "launch": ("one CUDA graph: 1 contraction + 1 persistent mixed-radius stencil and "
                        "1 scatter launch" if tuning["multi"] else
                        "one CUDA graph: 1 contraction + 1 stencil and 1 scatter launch per "

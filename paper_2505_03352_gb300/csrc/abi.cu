@@ -222,7 +222,10 @@ eps_status_t error_flag_ptr(int **out) {
 
 dim3 fwd_grid(const Geometry &g) { return dim3((g.ny + TJ - 1) / TJ, (g.nx + TI - 1) / TI); }
 long fwd_ntiles(const Geometry &g) { return (long)fwd_grid(g).x * fwd_grid(g).y; }
-dim3 bwd_grid(const Geometry &g) { return dim3((g.my + TB - 1) / TB, (g.mx + TA - 1) / TA); }
+// scatter tiles of TA x tbw subpixels (tbw: TB, or 64 for the batched calls' wide tiles)
+dim3 bwd_grid(const Geometry &g, int tbw = TB) {
+  return dim3((g.my + tbw - 1) / tbw, (g.mx + TA - 1) / TA);
+}
 
 // Dynamic shared memory of a forward launch: the stencil buffers, grown to
 // stage all of the tile's eps_hat components (up to 3) for one round of bulk
@@ -555,15 +558,19 @@ struct ScatterBoxes {
   int dbp, da, nci, ncj, ngj;
 };
 template <int RP1>
-ScatterBoxes scatter_boxes_t() {
+ScatterBoxes scatter_boxes_t(int tbw) {
+  if (tbw == 64) {
+    using S = BwdSmem<RP1, 64>;
+    return ScatterBoxes{S::DBP, S::DA_BOX, S::NCI, S::NCJ, S::NGJ};
+  }
   using S = BwdSmem<RP1>;
   return ScatterBoxes{S::DBP, S::DA_BOX, S::NCI, S::NCJ, S::NGJ};
 }
-ScatterBoxes scatter_boxes(int rp1) {
+ScatterBoxes scatter_boxes(int rp1, int tbw = TB) {
   switch (rp1) {
 #define EPSC_BOX_CASE(R) \
   case R:                \
-    return scatter_boxes_t<R>();
+    return scatter_boxes_t<R>(tbw);
     EPSC_BOX_CASE(1) EPSC_BOX_CASE(2) EPSC_BOX_CASE(3) EPSC_BOX_CASE(4) EPSC_BOX_CASE(5)
     EPSC_BOX_CASE(6) EPSC_BOX_CASE(7) EPSC_BOX_CASE(8) EPSC_BOX_CASE(9) EPSC_BOX_CASE(10)
     EPSC_BOX_CASE(11) EPSC_BOX_CASE(12)
@@ -579,11 +586,11 @@ ScatterBoxes scatter_boxes(int rp1) {
 // pitches not multiples of 16 bytes, radius class below 3); the kernel then
 // gathers element by element.
 bool scatter_maps(const Resolved &r, const float *seeds, const float *pd4, const float *ie2,
-                  CUtensorMap *maps) {
+                  CUtensorMap *maps, int tbw = TB) {
   PFN_encodeTiled enc = encode_tiled();
   const Geometry &g = r.g;
   if (!enc || r.rp1 < 3 || (g.my & 3) || (g.ny & 3)) return false;
-  const ScatterBoxes b = scatter_boxes(r.rp1);
+  const ScatterBoxes b = scatter_boxes(r.rp1, tbw);
   cuuint32_t es[3] = {1, 1, 1};
   for (int m = 0; m < 2; ++m) {
     cuuint64_t dims[3] = {(cuuint64_t)g.my, (cuuint64_t)g.mx, 1};
@@ -1077,6 +1084,7 @@ struct BatchTuning {
   int stage_comps;    // eps_hat components staged per round of bulk stores (1 or 3)
   int defer_seeds;    // 1: stencil writes seed factors, the seeds kernel applies W
   int bwd_bulk;       // grouped form: 1 = the scatter stages interior tiles by bulk copies
+  int bwd_cols;       // grouped form: scatter tile width in subpixels (32 or 64)
 };
 // Default: the grouped form, measured faster on the 64-region batch (radius
 // classes 2 .. 8): one kernel holding all twelve radius bodies runs them side
@@ -1084,7 +1092,7 @@ struct BatchTuning {
 // contraction blocks per SM streamed that batch's fields in 304 us against
 // 368 us with two; one eps_hat component per staging round took the call
 // from 0.916 to 0.897 ms.
-constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 3, 1, 0, 1};
+constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 3, 1, 0, 1, TB};
 // The TMA contraction's ring (2 stages of up to 6 x 32 x 64 floats) leaves
 // room for at most this many blocks per SM.
 constexpr int TMA_BATCH_MAX_BPS = 4;
@@ -1239,7 +1247,7 @@ eps_status_t run_fwd_grouped(const std::vector<Group> &gs, const std::vector<Res
 static_assert(sizeof(BwdTmaBatchArgs) <= 32764, "kernel parameter space");
 eps_status_t run_bwd_group_bulk(const Group &g, const std::vector<Resolved> &rs,
                                 const std::vector<BwdRegion> &regions, const KernelEntry &k,
-                                int *err, cudaStream_t s) {
+                                int tbw, int *err, cudaStream_t s) {
   std::unique_ptr<BwdTmaBatchArgs> ta(new BwdTmaBatchArgs);
   eps_status_t st = EPS_OK;
   for (size_t q0 = 0; q0 < g.regions.size() && st == EPS_OK; q0 += BWD_TMA_BATCH) {
@@ -1252,12 +1260,13 @@ eps_status_t run_bwd_group_bulk(const Group &g, const std::vector<Resolved> &rs,
     for (int q = 0; q < cnt; ++q) {
       const int ri = g.regions[q0 + q];
       const BwdRegion &br = regions[ri];
-      const dim3 grid = bwd_grid(rs[ri].g);
+      const dim3 grid = bwd_grid(rs[ri].g, tbw);
       ta->tile_start[q] = tiles;
       ta->tiles_j[q] = (int)grid.x;
       tiles += (int)(grid.x * grid.y);
       ta->r[q] = br;
-      ta->has_maps[q] = scatter_maps(rs[ri], br.seeds, br.pd4, br.ie2, &ta->maps[4 * q]) ? 1 : 0;
+      ta->has_maps[q] =
+          scatter_maps(rs[ri], br.seeds, br.pd4, br.ie2, &ta->maps[4 * q], tbw) ? 1 : 0;
     }
     ta->tile_start[cnt] = tiles;
     st = launch("eps_batched_scatter", k.fn, dim3((unsigned)tiles), k.smem, ta.get(), s, true);
@@ -1265,16 +1274,20 @@ eps_status_t run_bwd_group_bulk(const Group &g, const std::vector<Resolved> &rs,
   return st;
 }
 
+// tbw: scatter tile width in subpixels (TB, or 64: wide tiles, fewer
+// halo subpixels per output at two blocks per SM instead of three)
 eps_status_t run_bwd_grouped(const std::vector<Group> &gs, const std::vector<Resolved> &rs,
-                             const std::vector<BwdRegion> &regions, int bulk, int *err,
+                             const std::vector<BwdRegion> &regions, int bulk, int tbw, int *err,
                              cudaStream_t s) {
   BwdBatchArgs *ba = new BwdBatchArgs;
   eps_status_t st = EPS_OK;
+  const bool wide = tbw == 64;
   for (const Group &g : gs) {
     if (bulk) {
-      const KernelEntry kb = bwd_tma_batched_entry(g.rp1, g.bc);
+      const KernelEntry kb =
+          wide ? bwd_tma_batched_wide_entry(g.rp1, g.bc) : bwd_tma_batched_entry(g.rp1, g.bc);
       if (kb.fn) {
-        st = run_bwd_group_bulk(g, rs, regions, kb, err, s);
+        st = run_bwd_group_bulk(g, rs, regions, kb, tbw, err, s);
         if (st != EPS_OK) break;
         continue;
       }
@@ -1283,11 +1296,11 @@ eps_status_t run_bwd_grouped(const std::vector<Group> &gs, const std::vector<Res
     ba->n = (int)g.regions.size();
     ba->err = err;
     std::memcpy(ba->w, rs[g.regions[0]].w, sizeof(ba->w));
-    const KernelEntry k = bwd_entry(g.rp1, g.bc, true);
+    const KernelEntry k = wide ? bwd_batched_wide_entry(g.rp1, g.bc) : bwd_entry(g.rp1, g.bc, true);
     int tiles = 0;
     for (int q = 0; q < ba->n; ++q) {
       const int ri = g.regions[q];
-      const dim3 grid = bwd_grid(rs[ri].g);
+      const dim3 grid = bwd_grid(rs[ri].g, tbw);
       ba->tile_start[q] = tiles;
       ba->tiles_j[q] = (int)grid.x;
       tiles += (int)(grid.x * grid.y);
@@ -1386,7 +1399,7 @@ eps_status_t run_bwd_batch(const std::vector<Resolved> &rs, const eps_problem_t 
                            const std::vector<BwdRegion> &regions, const BatchTuning &t, int *err,
                            cudaStream_t s) {
   if (t.multi) return run_bwd_multi(make_sets(rs, probs), rs, regions, t.bwd_bps, err, s);
-  return run_bwd_grouped(make_groups(rs, probs), rs, regions, t.bwd_bulk, err, s);
+  return run_bwd_grouped(make_groups(rs, probs), rs, regions, t.bwd_bulk, t.bwd_cols, err, s);
 }
 
 eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float *const *C,
@@ -1574,11 +1587,12 @@ eps_status_t eps_batched_set_tuning(int32_t n, const eps_problem_t *probs, int32
       u.scatter_blocks_per_sm < 1 || u.scatter_blocks_per_sm > 16 || u.contract_blocks_per_sm < 1 ||
       u.contract_blocks_per_sm > 64 || (u.stage_components != 1 && u.stage_components != 3) ||
       (u.defer_seeds != 0 && u.defer_seeds != 1) ||
-      (u.scatter_bulk_staging != 0 && u.scatter_bulk_staging != 1))
+      (u.scatter_bulk_staging != 0 && u.scatter_bulk_staging != 1) ||
+      (u.scatter_tile_cols != 0 && u.scatter_tile_cols != 32 && u.scatter_tile_cols != 64))
     return EPS_ERR_INVALID_ARG;
   const BatchTuning t{u.multi, u.stencil_blocks_per_sm, u.scatter_blocks_per_sm,
                       u.contract_blocks_per_sm, u.stage_components, u.defer_seeds,
-                      u.scatter_bulk_staging};
+                      u.scatter_bulk_staging, u.scatter_tile_cols ? u.scatter_tile_cols : TB};
   store_tuning(batch_signature(n, probs, n_lambda), t);
   return EPS_OK;
 }
@@ -1627,19 +1641,20 @@ eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const f
   default_ms = best_ms;
   // coordinate descent over the launch form and shapes, two sweeps
   for (int sweep = 0; sweep < 2 && st == EPS_OK; ++sweep) {
-    for (int param = 0; param < 7 && st == EPS_OK; ++param) {
-      static const int values[7][4] = {{0, 1, -1, -1}, {1, 3, -1, -1}, {1, 2, 3, 4},
+    for (int param = 0; param < 8 && st == EPS_OK; ++param) {
+      static const int values[8][4] = {{0, 1, -1, -1}, {1, 3, -1, -1}, {1, 2, 3, 4},
                                        {1, 2, 3, 4},   {1, 2, 3, 4}, {0, 1, -1, -1},
-                                       {0, 1, -1, -1}};
+                                       {0, 1, -1, -1}, {32, 64, -1, -1}};
       for (int v = 0; v < 4 && st == EPS_OK; ++v) {
         const int val = values[param][v];
         if (val < 0) continue;
         BatchTuning t = best;
-        int *field[7] = {&t.multi, &t.stage_comps, &t.fwd_bps, &t.bwd_bps, &t.contract_bps,
-                         &t.defer_seeds, &t.bwd_bulk};
+        int *field[8] = {&t.multi, &t.stage_comps, &t.fwd_bps, &t.bwd_bps, &t.contract_bps,
+                         &t.defer_seeds, &t.bwd_bulk, &t.bwd_cols};
         if (*field[param] == val) continue;
         if ((param == 2 || param == 3) && !t.multi) continue;   // grouped form: one block per tile
-        if (param == 6 && t.multi) continue;                     // multi form: element-wise gather
+        // multi form: element-wise gather on TA x TB tiles
+        if ((param == 6 || param == 7) && t.multi) continue;
         *field[param] = val;
         float ms = 0.f;
         st = timeit(t, &ms);
@@ -1662,6 +1677,7 @@ eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const f
     result->stage_components = best.stage_comps;
     result->defer_seeds = best.defer_seeds;
     result->scatter_bulk_staging = best.bwd_bulk;
+    result->scatter_tile_cols = best.bwd_cols;
     result->evaluations = evals;
     result->default_ms = default_ms;
     result->tuned_ms = best_ms;

@@ -19,16 +19,18 @@
 
 namespace epsc {
 
-template <int RP1>
+// Shared-memory layout of a scatter tile of TA x TBW subpixels (TBW = TB,
+// 32, or the wide batched tiles' 64).
+template <int RP1, int TBW = TB>
 struct BwdSmem {
   static constexpr int R = RP1 - 1;
   static constexpr int GA_MAX = TA + 2 * R;                    // gather rows incl. fold halo
-  static constexpr int GB_MAX = TB + 2 * R;
+  static constexpr int GB_MAX = TBW + 2 * R;
   static constexpr int NSTRIP_MAX = (GA_MAX + NA_B - 1) / NA_B;
   static constexpr int DA_ALLOC = NSTRIP_MAX * NA_B + 2 * R;   // du rows readable by strips
-  static constexpr int DBP = TB + 4 * R;                       // du pitch
+  static constexpr int DBP = TBW + 4 * R;                      // du pitch
   static constexpr int NCI = (TA + 4 * R) / 2 + 3;             // cell rows covering du
-  static constexpr int NCJ0 = (TB + 4 * R) / 2 + 3;            // cell columns covering du
+  static constexpr int NCJ0 = (TBW + 4 * R) / 2 + 3;           // cell columns covering du
   // Row pitches of the cell maps leave room for a row that starts up to 3
   // floats after a 16-byte boundary (bulk tensor copies start on one).
   static constexpr int NCJ = (NCJ0 + 3 + 3) & ~3;
@@ -93,10 +95,10 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src) {
 // in the kernel parameters (bwd_tma_kernel: single region; the batched
 // bwd_tma_batched_kernel: the tile's region), or is null for a region whose
 // layout does not suit bulk copies; radius class 3 and up.
-template <int RP1, int BC, bool TMA = false, class Args>
+template <int RP1, int BC, bool TMA = false, int TBW = TB, class Args>
 __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, const int a0,
                                          const int b0, const CUtensorMap *maps = nullptr) {
-  using S = BwdSmem<RP1>;
+  using S = BwdSmem<RP1, TBW>;
   constexpr int R = S::R;
   constexpr int DBP = S::DBP;
   constexpr bool clamp = BC == EPS_BC_CLAMP;
@@ -111,7 +113,7 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
   const Geometry &g = rg.g;
   const int tid = threadIdx.x;
   const int ty = tid >> 5, tx = tid & 31;       // 8 x 32 thread grid for 2-D loops
-  const int aend = min(a0 + TA, g.mx), bend = min(b0 + TB, g.my);
+  const int aend = min(a0 + TA, g.mx), bend = min(b0 + TBW, g.my);
   // gather region: the tile, plus R extended positions where edge replicate folds
   const int ga_lo = a0 - ((clamp && a0 == 0) ? R : 0);
   const int ga_hi = aend + ((clamp && aend == g.mx) ? R : 0);
@@ -394,24 +396,25 @@ __global__ void __launch_bounds__(NTHREADS) bwd_tma_kernel(const __grid_constant
 }
 
 // Batched scatter of one radius group with bulk-copy staging: block b takes
-// tile b - tile_start[k] of region k, staged through region k's maps.
-template <int RP1, int BC>
+// tile b - tile_start[k] of region k (tiles of TA x TBW subpixels), staged
+// through region k's maps.
+template <int RP1, int BC, int TBW = TB>
 __global__ void __launch_bounds__(NTHREADS) bwd_tma_batched_kernel(const __grid_constant__ BwdTmaBatchArgs a) {
   int k, t;
   batch_tile(a, blockIdx.x, k, t);
   const int tj = a.tiles_j[k];
   const int ti = t / tj;
-  bwd_tile<RP1, BC, true>(a, a.r[k], ti * TA, (t - ti * tj) * TB,
-                          a.has_maps[k] ? &a.maps[4 * k] : nullptr);
+  bwd_tile<RP1, BC, true, TBW>(a, a.r[k], ti * TA, (t - ti * tj) * TBW,
+                               a.has_maps[k] ? &a.maps[4 * k] : nullptr);
 }
 
-template <int RP1, int BC>
+template <int RP1, int BC, int TBW = TB>
 __global__ void __launch_bounds__(NTHREADS) bwd_batched_kernel(const __grid_constant__ BwdBatchArgs a) {
   int k, t;
   batch_tile(a, blockIdx.x, k, t);
   const int tj = a.tiles_j[k];
   const int ti = t / tj;
-  bwd_tile<RP1, BC>(a, a.r[k], ti * TA, (t - ti * tj) * TB);
+  bwd_tile<RP1, BC, false, TBW>(a, a.r[k], ti * TA, (t - ti * tj) * TBW);
 }
 
 }  // namespace epsc

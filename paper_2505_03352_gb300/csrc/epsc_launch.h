@@ -24,6 +24,10 @@ KernelEntry bwd_tma_entry(int rp1, int bc);
 // The batched scatter of one radius group with bulk-copy staging (radius
 // classes 3 .. 12; {nullptr, 0} otherwise).
 KernelEntry bwd_tma_batched_entry(int rp1, int bc);
+// The batched scatter on wide tiles (TA x 64 subpixels): element-wise
+// staging (radius classes 1 .. 12) and bulk-copy staging (3 .. 12).
+KernelEntry bwd_batched_wide_entry(int rp1, int bc);
+KernelEntry bwd_tma_batched_wide_entry(int rp1, int bc);
 
 // Contraction kernel with 4 or 8 lanes per column.
 const void *contract_entry(int lanes);

@@ -116,6 +116,8 @@ def tuning(**kw):
     (dict(contract_blocks_per_sm=65), INVALID), (dict(stage_components=2), INVALID),
     (dict(defer_seeds=2), INVALID), (dict(scatter_bulk_staging=1), OK),
     (dict(scatter_bulk_staging=2), INVALID), (dict(scatter_bulk_staging=-1), INVALID),
+    (dict(scatter_tile_cols=64), OK), (dict(scatter_tile_cols=32), OK),
+    (dict(scatter_tile_cols=0), OK), (dict(scatter_tile_cols=48), INVALID),
 ])
 def test_set_tuning_ranges(L, kw, status):
     ps = [prob(), prob(mx=80)]

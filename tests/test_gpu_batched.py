@@ -163,6 +163,8 @@ def test_autotuned_shapes_give_identical_results():
     dict(multi=1, defer_seeds=1, contract_blocks_per_sm=2),
     dict(multi=0, scatter_bulk_staging=0),                # scatter gathers element by element
     dict(multi=0, scatter_bulk_staging=1, stage_components=3),   # bulk-copy scatter staging
+    dict(multi=0, scatter_tile_cols=64, scatter_bulk_staging=0),  # wide scatter tiles
+    dict(multi=0, scatter_tile_cols=64, scatter_bulk_staging=1),
 ])
 def test_every_launch_form_equals_per_region_calls(shapes):
     import paper_2505_03352_gb300 as ec
