@@ -210,3 +210,48 @@ def test_packed_field_buffers_must_hold_the_packed_size(rec, monkeypatch):
     with pytest.raises(ValueError, match="100 are needed"):
         eb.eps_vjp(P, C, [ok], [ok[:99]], field_type=eb.EPS_FIELD_F16X2_SCALED)
     assert launches(rec) == ["eps_vjp"]
+
+
+def test_surrogate_call_reaches_the_library_and_checks_its_value_buffer(rec):
+    # eps_vjp_surrogate: the S buffer is a float64 0-d tensor on the call's
+    # device (allocated if not given); a wrong dtype or shape raises first
+    C = _C()
+    EF, EA = _fields(2)
+    g, e, S = eb.eps_vjp_surrogate(P, C, EF, EA, eps_out=True)
+    name, args = rec[-1]
+    assert name == "eps_vjp_surrogate"
+    assert S.dtype == torch.float64 and S.shape == ()
+    assert _val(args[1]) == C.data_ptr() and _val(args[10]) == S.data_ptr()
+    assert _val(args[8]) == g.data_ptr() and _val(args[9]) == e.data_ptr()
+    g, S2 = eb.eps_vjp_surrogate(P, C, EF, EA)
+    assert _val(rec[-1][1][9]) is None
+    n = len(launches(rec))
+    for bad in (torch.zeros((), dtype=torch.float32), torch.zeros(1, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            eb.eps_vjp_surrogate(P, C, EF, EA, S=bad)
+    with pytest.raises(ValueError):
+        eb.eps_vjp_surrogate(P, C, EF, EA[:1])
+    assert len(launches(rec)) == n
+
+
+def test_prepared_surrogate_marshals_the_fields_once(rec):
+    # autograd.AdjointSurrogate: the field pointer arrays and the workspace
+    # are built at construction; each call passes C's pointer and fresh
+    # outputs, and a C of the wrong shape raises before any launch
+    from paper_2505_03352_gb300 import autograd as ag
+    EF, EA = _fields(3)
+    surr = ag.AdjointSurrogate(P, EF, EA, with_eps=True)
+    C = _C()
+    dJdC, eps, S = surr.call(C)
+    name, args = rec[-1]
+    assert name == "eps_vjp_surrogate" and args[2] == 3
+    assert [args[4][l] for l in range(3)] == [t.data_ptr() for t in EF]
+    assert [args[5][l] for l in range(3)] == [t.data_ptr() for t in EA]
+    assert _val(args[1]) == C.data_ptr() and _val(args[9]) == eps.data_ptr()
+    ws_ptr = _val(args[11])
+    surr.call(C)
+    assert _val(rec[-1][1][11]) == ws_ptr          # the same workspace every call
+    n = len(launches(rec))
+    with pytest.raises(ValueError):
+        surr.call(torch.rand((P.mx + 2, P.my)))
+    assert len(launches(rec)) == n
