@@ -790,15 +790,22 @@ def run_variants(torch, ec, synth, dev, flush_l2,
         with torch.cuda.graph(graph):
             bv()
         ms_b = _timed(graph.replay, flush_l2, 20, torch)
-        # the other scatter tile shape, forced (the tuner's pick stays cached
-        # for the graph above)
-        alt_cols = 64 if tuning.get("scatter_tile_cols", 32) == 32 else 32
-        shapes = {k: tuning[k] for k in ("multi", "stencil_blocks_per_sm", "scatter_blocks_per_sm",
-                                         "contract_blocks_per_sm", "stage_components",
-                                         "defer_seeds", "scatter_bulk_staging")}
-        bv.set_tuning(**shapes, scatter_tile_cols=alt_cols)
-        ms_alt = _timed(bv, flush_l2, 20, torch)
-        bv.set_tuning(**shapes, scatter_tile_cols=tuning.get("scatter_tile_cols", 32))
+        # the alternatives the tuner passed over, forced one at a time (no
+        # graph; the tuner's pick is restored for anything after)
+        keys = ("multi", "stencil_blocks_per_sm", "scatter_blocks_per_sm", "contract_blocks_per_sm",
+                "stage_components", "defer_seeds", "scatter_bulk_staging", "scatter_tile_cols",
+                "concurrent_groups")
+        picked = {k: tuning.get(k, 0) for k in keys}
+        alternatives = {}
+        for name, change in (
+                ("scatter_tile_cols", {"scatter_tile_cols": 64 if picked["scatter_tile_cols"] in (0, 32)
+                                       else 32}),
+                ("concurrent_groups", {"concurrent_groups": 1 - picked["concurrent_groups"]})):
+            if picked["multi"]:
+                continue
+            bv.set_tuning(**dict(picked, **change))
+            alternatives[name] = dict(change, ms_per_call=round(_timed(bv, flush_l2, 20, torch), 4))
+        bv.set_tuning(**picked)
         singles = [ec.PreparedVjp(p, C, ef, ea, G, eps_out=E)
                    for p, C, ef, ea, G, E in zip(probs, Cs, EFs, EAs, bv.dJdC, bv.eps)]
 
@@ -816,8 +823,8 @@ def run_variants(torch, ec, synth, dev, flush_l2,
                 "value": vox / (ms_s * 1e-3), "ms_per_call": round(ms_s, 4)},
             "speedup_vs_per_region": round(ms_s / ms_b, 3),
             "default_shapes_ms_per_call": round(ms_default, 4), "autotuned": tuning,
-            "other_scatter_tile": {"cols": alt_cols, "ms_per_call": round(ms_alt, 4),
-                                   "note": "same shapes, the other scatter tile width, no graph"},
+            "alternatives": dict(alternatives, note=("the tuned shapes with one field changed, "
+                                                     "timed without a graph")),
             "launch": ("one CUDA graph: 1 contraction + 1 persistent mixed-radius stencil and "
                        "1 scatter launch" if tuning["multi"] else
                        "one CUDA graph: 1 contraction + 1 stencil and 1 scatter launch per "

@@ -240,7 +240,7 @@ typedef struct {
   int32_t multi, stencil_blocks_per_sm, scatter_blocks_per_sm, contract_blocks_per_sm;
   int32_t stage_components, defer_seeds, evaluations;
   float default_ms, tuned_ms;
-  int32_t scatter_bulk_staging, scatter_tile_cols;
+  int32_t scatter_bulk_staging, scatter_tile_cols, concurrent_groups;
 } eps_tuning_t;
 
 /*
@@ -250,13 +250,21 @@ typedef struct {
  * it applies to, or -1 for eps_forward_batched.  Fields: multi 0 or 1,
  * blocks per SM 1 .. 16 (stencil, scatter) and 1 .. 64 (contraction),
  * stage_components 1 or 3, defer_seeds 0 or 1, scatter_bulk_staging 0 or 1,
- * scatter_tile_cols 0 (= 32), 32 or 64; else EPS_ERR_INVALID_ARG.
+ * scatter_tile_cols 0 (= 32), 32 or 64, concurrent_groups 0 or 1; else
+ * EPS_ERR_INVALID_ARG.
  * scatter_bulk_staging (grouped form, radius classes 3 and up): 1 stages the
  * scatter's interior tiles through bulk tensor copies (each launch carries
  * up to 32 regions' tensor maps in its parameters), 0 gathers element by
  * element.  scatter_tile_cols (grouped form): the scatter's tile shape,
  * 32 x 32 or 32 x 64 control subpixels (the wide tile recomputes fewer halo
  * subpixels per output but fits two blocks on an SM instead of three).
+ * concurrent_groups (grouped form): 1 puts each radius group's stencil and
+ * scatter launches on an auxiliary stream of their own (one set of up to 8
+ * per device, created on first use and kept for the process; forked from and
+ * joined back to `stream` with events, so stream order and graph capture of
+ * `stream` hold), the stencils writing seed factors beside the contraction
+ * and a seeds launch on `stream` applying the column sums; calls from
+ * several host threads share the set and enqueue one after another.
  * The contraction streams the fields of every region through bulk tensor
  * copies (up to 4 blocks per SM, so larger values act as 4) when the batch
  * needs at most 192 tensor maps (n * n_lambda * 2); larger batches use

@@ -1085,6 +1085,7 @@ struct BatchTuning {
   int defer_seeds;    // 1: stencil writes seed factors, the seeds kernel applies W
   int bwd_bulk;       // grouped form: 1 = the scatter stages interior tiles by bulk copies
   int bwd_cols;       // grouped form: scatter tile width in subpixels (32 or 64)
+  int group_streams;  // grouped form: 1 = each radius group's launches on a stream of its own
 };
 // Default: the grouped form, measured faster on the 64-region batch (radius
 // classes 2 .. 8): one kernel holding all twelve radius bodies runs them side
@@ -1092,7 +1093,7 @@ struct BatchTuning {
 // contraction blocks per SM streamed that batch's fields in 304 us against
 // 368 us with two; one eps_hat component per staging round took the call
 // from 0.916 to 0.897 ms.
-constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 3, 1, 0, 1, TB};
+constexpr BatchTuning DEFAULT_TUNING{0, 3, 3, 3, 1, 0, 1, TB, 0};
 // The TMA contraction's ring (2 stages of up to 6 x 32 x 64 floats) leaves
 // room for at most this many blocks per SM.
 constexpr int TMA_BATCH_MAX_BPS = 4;
@@ -1208,12 +1209,16 @@ std::vector<LaunchSet> make_sets(const std::vector<Resolved> &rs, const eps_prob
 }
 
 // Grouped form: one batched stencil launch per group.
+// gstreams (optional): the stream of each group's launch (concurrent form)
 eps_status_t run_fwd_grouped(const std::vector<Group> &gs, const std::vector<Resolved> &rs,
                              const std::vector<FwdRegion> &regions, int ncomp, int *err,
-                             cudaStream_t s, bool pdl) {
+                             cudaStream_t s, bool pdl,
+                             const std::vector<cudaStream_t> *gstreams = nullptr) {
   FwdBatchArgs *ba = new FwdBatchArgs;
   eps_status_t st = EPS_OK;
-  for (const Group &g : gs) {
+  for (size_t gi = 0; gi < gs.size(); ++gi) {
+    const Group &g = gs[gi];
+    const cudaStream_t gst = gstreams ? (*gstreams)[gi] : s;
     std::memset(ba, 0, sizeof(*ba));
     ba->n = (int)g.regions.size();
     ba->err = err;
@@ -1233,7 +1238,8 @@ eps_status_t run_fwd_grouped(const std::vector<Group> &gs, const std::vector<Res
     }
     ba->tile_start[ba->n] = tiles;
     for (int q = 0; q < ba->n; ++q) ba->r[q].stage_floats = (int)(smem / sizeof(float));
-    st = launch("eps_batched_stencil", k.fn, dim3((unsigned)tiles), smem, ba, s, pdl);
+    st = launch("eps_batched_stencil", k.fn, dim3((unsigned)tiles), smem, ba, gst,
+                pdl && !gstreams);
     if (st != EPS_OK) break;
   }
   delete ba;
@@ -1247,7 +1253,7 @@ eps_status_t run_fwd_grouped(const std::vector<Group> &gs, const std::vector<Res
 static_assert(sizeof(BwdTmaBatchArgs) <= 32764, "kernel parameter space");
 eps_status_t run_bwd_group_bulk(const Group &g, const std::vector<Resolved> &rs,
                                 const std::vector<BwdRegion> &regions, const KernelEntry &k,
-                                int tbw, int *err, cudaStream_t s) {
+                                int tbw, int *err, cudaStream_t s, bool pdl) {
   std::unique_ptr<BwdTmaBatchArgs> ta(new BwdTmaBatchArgs);
   eps_status_t st = EPS_OK;
   for (size_t q0 = 0; q0 < g.regions.size() && st == EPS_OK; q0 += BWD_TMA_BATCH) {
@@ -1269,7 +1275,7 @@ eps_status_t run_bwd_group_bulk(const Group &g, const std::vector<Resolved> &rs,
           scatter_maps(rs[ri], br.seeds, br.pd4, br.ie2, &ta->maps[4 * q], tbw) ? 1 : 0;
     }
     ta->tile_start[cnt] = tiles;
-    st = launch("eps_batched_scatter", k.fn, dim3((unsigned)tiles), k.smem, ta.get(), s, true);
+    st = launch("eps_batched_scatter", k.fn, dim3((unsigned)tiles), k.smem, ta.get(), s, pdl);
   }
   return st;
 }
@@ -1278,16 +1284,19 @@ eps_status_t run_bwd_group_bulk(const Group &g, const std::vector<Resolved> &rs,
 // halo subpixels per output at two blocks per SM instead of three)
 eps_status_t run_bwd_grouped(const std::vector<Group> &gs, const std::vector<Resolved> &rs,
                              const std::vector<BwdRegion> &regions, int bulk, int tbw, int *err,
-                             cudaStream_t s) {
+                             cudaStream_t s,
+                             const std::vector<cudaStream_t> *gstreams = nullptr) {
   BwdBatchArgs *ba = new BwdBatchArgs;
   eps_status_t st = EPS_OK;
   const bool wide = tbw == 64;
-  for (const Group &g : gs) {
+  for (size_t gi = 0; gi < gs.size(); ++gi) {
+    const Group &g = gs[gi];
+    const cudaStream_t gst = gstreams ? (*gstreams)[gi] : s;
     if (bulk) {
       const KernelEntry kb =
           wide ? bwd_tma_batched_wide_entry(g.rp1, g.bc) : bwd_tma_batched_entry(g.rp1, g.bc);
       if (kb.fn) {
-        st = run_bwd_group_bulk(g, rs, regions, kb, tbw, err, s);
+        st = run_bwd_group_bulk(g, rs, regions, kb, tbw, err, gst, !gstreams);
         if (st != EPS_OK) break;
         continue;
       }
@@ -1307,7 +1316,7 @@ eps_status_t run_bwd_grouped(const std::vector<Group> &gs, const std::vector<Res
       ba->r[q] = regions[ri];
     }
     ba->tile_start[ba->n] = tiles;
-    st = launch("eps_batched_scatter", k.fn, dim3((unsigned)tiles), k.smem, ba, s, true);
+    st = launch("eps_batched_scatter", k.fn, dim3((unsigned)tiles), k.smem, ba, gst, !gstreams);
     if (st != EPS_OK) break;
   }
   delete ba;
@@ -1402,6 +1411,59 @@ eps_status_t run_bwd_batch(const std::vector<Resolved> &rs, const eps_problem_t 
   return run_bwd_grouped(make_groups(rs, probs), rs, regions, t.bwd_bulk, t.bwd_cols, err, s);
 }
 
+// Auxiliary streams of the concurrent grouped form: one set per device,
+// created on first use and kept for the process.  A call forks them from the
+// caller's stream with an event and joins them back before it returns, so
+// ordering against other work on the caller's stream (and graph capture of
+// that stream) is kept; the mutex makes the enqueue sequences of calls from
+// different host threads, which share the set, follow one another.
+constexpr int AUX_STREAMS = 8;
+struct AuxSet {
+  bool ready = false;
+  cudaStream_t st[AUX_STREAMS];
+  cudaEvent_t fork, mid, join[AUX_STREAMS], join2[AUX_STREAMS];
+};
+std::mutex g_aux_mu;
+AuxSet g_aux[64];
+
+eps_status_t aux_set(AuxSet **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return EPS_ERR_CUDA;
+  AuxSet &a = g_aux[dev];
+  if (!a.ready) {
+    for (int i = 0; i < AUX_STREAMS; ++i) {
+      if (cudaStreamCreateWithFlags(&a.st[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&a.join[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&a.join2[i], cudaEventDisableTiming) != cudaSuccess)
+        return EPS_ERR_CUDA;
+    }
+    if (cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.mid, cudaEventDisableTiming) != cudaSuccess)
+      return EPS_ERR_CUDA;
+    a.ready = true;
+  }
+  *out = &a;
+  return EPS_OK;
+}
+
+// Every stream in `waiters` waits for the work enqueued so far on `s`.
+eps_status_t fork_streams(cudaStream_t s, cudaEvent_t ev, const cudaStream_t *waiters, int n) {
+  if (cudaEventRecord(ev, s) != cudaSuccess) return EPS_ERR_CUDA;
+  for (int i = 0; i < n; ++i)
+    if (cudaStreamWaitEvent(waiters[i], ev, 0) != cudaSuccess) return EPS_ERR_CUDA;
+  return EPS_OK;
+}
+
+// `s` waits for the work enqueued so far on every stream in `workers`.
+eps_status_t join_streams(cudaStream_t s, const cudaEvent_t *evs, const cudaStream_t *workers,
+                          int n) {
+  for (int i = 0; i < n; ++i) {
+    if (cudaEventRecord(evs[i], workers[i]) != cudaSuccess) return EPS_ERR_CUDA;
+    if (cudaStreamWaitEvent(s, evs[i], 0) != cudaSuccess) return EPS_ERR_CUDA;
+  }
+  return EPS_OK;
+}
+
 eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float *const *C,
                               int32_t n_lambda, int32_t field_type, const void *const *EF,
                               const void *const *EA, const float *field_scales, float scale,
@@ -1484,7 +1546,8 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
     fr[k].g = g;
     fr[k].mode = MODE_C64;
     fr[k].write_eps = out_eps ? 1 : 0;
-    fr[k].defer_seeds = t.defer_seeds;
+    // the concurrent form's stencils never wait for the contraction
+    fr[k].defer_seeds = (t.defer_seeds || (t.group_streams && !t.multi)) ? 1 : 0;
     fr[k].C = C[k];
     fr[k].eps = out_eps;
     fr[k].W = Wm;
@@ -1501,6 +1564,25 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
   ca->err = err;
   sa->ncol = ncol;
   sa->err = err;
+  // Concurrent grouped form: each radius group's stencil and scatter launches
+  // go to an auxiliary stream of their own, so the groups' partial waves run
+  // side by side.  The stencils (seed factors only) start with the
+  // contraction; the seeds kernel runs on `s` once the contraction and every
+  // stencil are done; then the scatters run on the auxiliary streams again.
+  const bool conc = t.group_streams && !t.multi;
+  std::unique_lock<std::mutex> aux_lock(g_aux_mu, std::defer_lock);
+  AuxSet *aux = nullptr;
+  std::vector<Group> groups;
+  std::vector<cudaStream_t> gstreams;
+  int naux = 0;
+  if (conc) {
+    aux_lock.lock();
+    if ((st = aux_set(&aux)) != EPS_OK) return st;
+    groups = make_groups(rs, probs);
+    naux = (int)std::min<size_t>(groups.size(), AUX_STREAMS);
+    for (size_t gi = 0; gi < groups.size(); ++gi) gstreams.push_back(aux->st[gi % AUX_STREAMS]);
+    if (naux > 0 && (st = fork_streams(s, aux->fork, aux->st, naux)) != EPS_OK) return st;
+  }
   if (ncol > 0) {
     int nsm = 0;
     if ((st = sm_count(&nsm)) != EPS_OK) return st;
@@ -1523,6 +1605,17 @@ eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float
   if (st != EPS_OK) return st;
   bool any_eps = false;
   for (int k = 0; k < n; ++k) any_eps = any_eps || (eps_out && eps_out[k]);
+  if (conc) {
+    const int nc = std::min(any_eps ? 3 : 0, t.stage_comps);
+    if ((st = run_fwd_grouped(groups, rs, fr, nc, err, s, false, &gstreams)) != EPS_OK) return st;
+    if ((st = join_streams(s, aux->join, aux->st, naux)) != EPS_OK) return st;
+    if ((st = run_seeds(*sa, s)) != EPS_OK) return st;
+    if (naux > 0 && (st = fork_streams(s, aux->mid, aux->st, naux)) != EPS_OK) return st;
+    if ((st = run_bwd_grouped(groups, rs, br, t.bwd_bulk, t.bwd_cols, err, s, &gstreams)) !=
+        EPS_OK)
+      return st;
+    return join_streams(s, aux->join2, aux->st, naux);
+  }
   st = run_fwd_batch(rs, probs, fr, any_eps ? 3 : 0, t, err, s, true);
   if (st == EPS_OK && t.defer_seeds) st = run_seeds(*sa, s);
   if (st != EPS_OK) return st;
@@ -1588,11 +1681,13 @@ eps_status_t eps_batched_set_tuning(int32_t n, const eps_problem_t *probs, int32
       u.contract_blocks_per_sm > 64 || (u.stage_components != 1 && u.stage_components != 3) ||
       (u.defer_seeds != 0 && u.defer_seeds != 1) ||
       (u.scatter_bulk_staging != 0 && u.scatter_bulk_staging != 1) ||
-      (u.scatter_tile_cols != 0 && u.scatter_tile_cols != 32 && u.scatter_tile_cols != 64))
+      (u.scatter_tile_cols != 0 && u.scatter_tile_cols != 32 && u.scatter_tile_cols != 64) ||
+      (u.concurrent_groups != 0 && u.concurrent_groups != 1))
     return EPS_ERR_INVALID_ARG;
   const BatchTuning t{u.multi, u.stencil_blocks_per_sm, u.scatter_blocks_per_sm,
                       u.contract_blocks_per_sm, u.stage_components, u.defer_seeds,
-                      u.scatter_bulk_staging, u.scatter_tile_cols ? u.scatter_tile_cols : TB};
+                      u.scatter_bulk_staging, u.scatter_tile_cols ? u.scatter_tile_cols : TB,
+                      u.concurrent_groups};
   store_tuning(batch_signature(n, probs, n_lambda), t);
   return EPS_OK;
 }
@@ -1641,20 +1736,20 @@ eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const f
   default_ms = best_ms;
   // coordinate descent over the launch form and shapes, two sweeps
   for (int sweep = 0; sweep < 2 && st == EPS_OK; ++sweep) {
-    for (int param = 0; param < 8 && st == EPS_OK; ++param) {
-      static const int values[8][4] = {{0, 1, -1, -1}, {1, 3, -1, -1}, {1, 2, 3, 4},
+    for (int param = 0; param < 9 && st == EPS_OK; ++param) {
+      static const int values[9][4] = {{0, 1, -1, -1}, {1, 3, -1, -1}, {1, 2, 3, 4},
                                        {1, 2, 3, 4},   {1, 2, 3, 4}, {0, 1, -1, -1},
-                                       {0, 1, -1, -1}, {32, 64, -1, -1}};
+                                       {0, 1, -1, -1}, {32, 64, -1, -1}, {0, 1, -1, -1}};
       for (int v = 0; v < 4 && st == EPS_OK; ++v) {
         const int val = values[param][v];
         if (val < 0) continue;
         BatchTuning t = best;
-        int *field[8] = {&t.multi, &t.stage_comps, &t.fwd_bps, &t.bwd_bps, &t.contract_bps,
-                         &t.defer_seeds, &t.bwd_bulk, &t.bwd_cols};
+        int *field[9] = {&t.multi, &t.stage_comps, &t.fwd_bps, &t.bwd_bps, &t.contract_bps,
+                         &t.defer_seeds, &t.bwd_bulk, &t.bwd_cols, &t.group_streams};
         if (*field[param] == val) continue;
         if ((param == 2 || param == 3) && !t.multi) continue;   // grouped form: one block per tile
-        // multi form: element-wise gather on TA x TB tiles
-        if ((param == 6 || param == 7) && t.multi) continue;
+        // multi form: element-wise gather on TA x TB tiles, one stream
+        if ((param == 6 || param == 7 || param == 8) && t.multi) continue;
         *field[param] = val;
         float ms = 0.f;
         st = timeit(t, &ms);
@@ -1678,6 +1773,7 @@ eps_status_t eps_autotune_batched(int32_t n, const eps_problem_t *probs, const f
     result->defer_seeds = best.defer_seeds;
     result->scatter_bulk_staging = best.bwd_bulk;
     result->scatter_tile_cols = best.bwd_cols;
+    result->concurrent_groups = best.group_streams;
     result->evaluations = evals;
     result->default_ms = default_ms;
     result->tuned_ms = best_ms;

@@ -518,12 +518,12 @@ class BatchedVjp:
         """Store launch shapes for this batch (eps_batched_set_tuning); keys are
         the eps_tuning_t fields multi, stencil_blocks_per_sm,
         scatter_blocks_per_sm, contract_blocks_per_sm, stage_components,
-        defer_seeds, scatter_bulk_staging and scatter_tile_cols (defaults: the
-        library's default shapes)."""
+        defer_seeds, scatter_bulk_staging, scatter_tile_cols and
+        concurrent_groups (defaults: the library's default shapes)."""
         r = eps_tuning_t()
         base = dict(multi=0, stencil_blocks_per_sm=3, scatter_blocks_per_sm=3,
                     contract_blocks_per_sm=3, stage_components=1, defer_seeds=0,
-                    scatter_bulk_staging=1, scatter_tile_cols=32)
+                    scatter_bulk_staging=1, scatter_tile_cols=32, concurrent_groups=0)
         base.update(shapes)
         for k, v in base.items():
             setattr(r, k, int(v))
@@ -546,7 +546,8 @@ class eps_tuning_t(ctypes.Structure):
                 ("stage_components", ctypes.c_int32), ("defer_seeds", ctypes.c_int32),
                 ("evaluations", ctypes.c_int32),
                 ("default_ms", ctypes.c_float), ("tuned_ms", ctypes.c_float),
-                ("scatter_bulk_staging", ctypes.c_int32), ("scatter_tile_cols", ctypes.c_int32)]
+                ("scatter_bulk_staging", ctypes.c_int32), ("scatter_tile_cols", ctypes.c_int32),
+                ("concurrent_groups", ctypes.c_int32)]
 
 
 def eps_sync_status(stream=None):

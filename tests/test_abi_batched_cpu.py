@@ -118,6 +118,7 @@ def tuning(**kw):
     (dict(scatter_bulk_staging=2), INVALID), (dict(scatter_bulk_staging=-1), INVALID),
     (dict(scatter_tile_cols=64), OK), (dict(scatter_tile_cols=32), OK),
     (dict(scatter_tile_cols=0), OK), (dict(scatter_tile_cols=48), INVALID),
+    (dict(concurrent_groups=1), OK), (dict(concurrent_groups=2), INVALID),
 ])
 def test_set_tuning_ranges(L, kw, status):
     ps = [prob(), prob(mx=80)]

@@ -107,6 +107,37 @@ def test_batched_call_in_a_cuda_graph():
         torch.testing.assert_close(E0[k], refe[k], rtol=0, atol=0)
 
 
+def test_concurrent_groups_in_a_cuda_graph():
+    # the concurrent form forks its auxiliary streams from the captured stream
+    # and joins them back: the capture is valid and each replay equals the
+    # direct call (the auxiliary set is created by the first, uncaptured call)
+    import torch
+
+    import paper_2505_03352_gb300 as ec
+    probs, Cs, EF, EA, _ = inputs(region_set(n=10, seed=51))
+    bv = ec.BatchedVjp(probs, Cs, EF, EA)
+    bv.set_tuning(concurrent_groups=1)
+    G0, E0 = bv()
+    ec.eps_sync_status()
+    ref_g = [g.clone() for g in G0]
+    ref_e = [e.clone() for e in E0]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        bv()
+    for k in range(len(probs)):
+        bv.dJdC[k].fill_(float("nan"))
+        bv.eps[k].fill_(float("nan"))
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        ec.eps_sync_status()
+        for k in range(len(probs)):
+            torch.testing.assert_close(bv.dJdC[k], ref_g[k], rtol=0, atol=0)
+            torch.testing.assert_close(bv.eps[k], ref_e[k], rtol=0, atol=0)
+
+
 def test_mixed_radius_classes_need_their_own_launch_set():
     # radii 5.5 and 6 share the radius class ceil(R) = 6: the batch takes an
     # extra launch set, and both match their per-region calls
@@ -165,6 +196,8 @@ def test_autotuned_shapes_give_identical_results():
     dict(multi=0, scatter_bulk_staging=1, stage_components=3),   # bulk-copy scatter staging
     dict(multi=0, scatter_tile_cols=64, scatter_bulk_staging=0),  # wide scatter tiles
     dict(multi=0, scatter_tile_cols=64, scatter_bulk_staging=1),
+    dict(multi=0, concurrent_groups=1),                   # radius groups on streams of their own
+    dict(multi=0, concurrent_groups=1, scatter_bulk_staging=0, scatter_tile_cols=64),
 ])
 def test_every_launch_form_equals_per_region_calls(shapes):
     import paper_2505_03352_gb300 as ec
