@@ -286,6 +286,51 @@ PFN_encodeTiled encode_tiled() {
   return fn;
 }
 
+// Tensor map of eps_hat [3][nx][ny][nz] for the stencil's swizzled staging
+// form: a {nz, ny, nx, 3} float tensor with a {nz, TJ, TI, 1} box and the
+// 128-byte swizzle.  nz = 32 only (a column's planes are exactly one
+// swizzle row); false otherwise or when the map cannot be made (the plain
+// staging then runs).
+bool eps_store_map(const Geometry &g, float *eps, CUtensorMap *map) {
+  PFN_encodeTiled enc = encode_tiled();
+  if (!enc || !eps || g.nz != 32 || !aligned(eps, 16)) return false;
+  const cuuint64_t col = (cuuint64_t)g.nz * 4;
+  cuuint64_t dims[4] = {(cuuint64_t)g.nz, (cuuint64_t)g.ny, (cuuint64_t)g.nx, 3};
+  cuuint64_t strides[3] = {col, col * g.ny, col * g.ny * g.nx};
+  cuuint32_t box[4] = {(cuuint32_t)g.nz, (cuuint32_t)TJ, (cuuint32_t)TI, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)eps, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Dynamic shared memory of a single-region forward launch that stages
+// `ncomp` (1 .. 3) eps_hat components through the swizzled form: the
+// stencil buffers or the staging buffers, whichever is larger, plus 1 KB
+// so that the staging can start on a 1024-byte boundary.
+size_t fwd_smem_swizzled(const KernelEntry &k, const Geometry &g, int ncomp, int *stage_floats) {
+  const int comp_floats = TI * TJ * g.nz;
+  ncomp = std::max(1, std::min(ncomp, 3));
+  *stage_floats = ncomp * comp_floats;
+  return std::max(k.smem, sizeof(float) * ncomp * comp_floats + 1024);
+}
+
+// Sets up the eps_hat output of a single-region forward launch: the
+// swizzled staging form (tensor map in `fa`) where eps_store_map allows,
+// else plain staging of `ncomp` components per round (ncomp 0: direct
+// stores, nz a multiple of 4); returns the launch's dynamic shared memory.
+size_t fwd_eps_output(FwdArgs &fa, const KernelEntry &k, const Geometry &g, int ncomp,
+                      int swz_comps) {
+  if (swz_comps > 0 && !fa.r.write_offdiag && eps_store_map(g, fa.r.eps, &fa.eps_map)) {
+    fa.r.eps_tma = 1;
+    fa.r.direct_eps = 0;
+    return fwd_smem_swizzled(k, g, swz_comps, &fa.r.stage_floats);
+  }
+  fa.r.eps_tma = 0;
+  fa.r.direct_eps = (ncomp == 0 && (g.nz & 3) == 0) ? 1 : 0;
+  return fwd_smem(k, g, fa.r.direct_eps ? 0 : std::max(ncomp, 1), &fa.r.stage_floats);
+}
+
 // J-support window of a column in floats: the 32-byte sectors holding
 // planes k0 .. k0+nk (complex64, 8 bytes per plane).
 void support_window(const Geometry &g, int *x0, int *bx) {
@@ -529,6 +574,8 @@ constexpr StencilForm FORM_ONE_WAVE{0, 3};
 // (stage_comps 0) measured no better in the fused calls (BF16 1.25 ms,
 // 600 x 600 call 47.6 against 44.3 us), so the fused forms keep staging.
 constexpr StencilForm FORM_MULTI_WAVE{1, 1};
+// eps_forward's swizzled staging (nz = 32): eps_hat buffers per block
+constexpr int FWD_SWZ_COMPS = 1;
 
 eps_status_t stencil_form(const Geometry &g, StencilForm *f, long *blocks) {
   int nsm = 0;
@@ -702,16 +749,18 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps, 
   fa.r.eps = eps;
   fa.r.offdiag = od ? offdiag : nullptr;
   const KernelEntry k = fwd_entry(r.rp1, r.g.bc);
-  // More than one wave of tiles: eps_hat leaves by warp-cooperative direct
-  // stores (no staging, only the stencil's 31 KB of shared memory); within
-  // one wave, one component staged per round.  Measured on a GB300: the
-  // 2000 x 2000 forward 197 us (three components staged) -> 154 us (one) ->
-  // 136 us (direct); the 600 x 600 forward 19.2 us staged, 21.2 us direct.
+  // nz = 32: swizzled staging through one buffer (FWD_SWZ_COMPS).
+  // Otherwise, more than one wave of tiles: eps_hat leaves by
+  // warp-cooperative direct stores (no staging, only the stencil's 31 KB of
+  // shared memory); within one wave, one component staged per round.
+  // Measured on a GB300, the 2000 x 2000 forward (nz = 32): three
+  // components staged plainly 197 us, one 154 us, direct stores 136 us,
+  // swizzled staging through one buffer 101 us (two 106 us, three 134 us);
+  // the 600 x 600 forward (nz = 24) 19.2 us staged, 21.2 us direct.
   int nsm = 0;
   if ((st = sm_count(&nsm)) != EPS_OK) return st;
-  const bool direct = fwd_ntiles(r.g) > (long)ONE_WAVE_TILES_PER_SM * nsm && (r.g.nz & 3) == 0;
-  fa.r.direct_eps = direct ? 1 : 0;
-  const size_t smem = fwd_smem(k, r.g, direct ? 0 : (od ? 5 : 1), &fa.r.stage_floats);
+  const bool multi = fwd_ntiles(r.g) > (long)ONE_WAVE_TILES_PER_SM * nsm;
+  const size_t smem = fwd_eps_output(fa, k, r.g, multi ? 0 : (od ? 5 : 1), FWD_SWZ_COMPS);
   return launch("eps_forward", k.fn, dim3((unsigned)fwd_ntiles(r.g)), smem, &fa, (cudaStream_t)stream);
 }
 
@@ -833,9 +882,9 @@ eps_status_t vjp_fused(const eps_problem_t *prob, const float *C, int32_t n_lamb
     fa.r.epsc = form.defer ? epsc : nullptr;
   }
   const KernelEntry kf = fwd_entry(r.rp1, r.g.bc);
-  fa.r.direct_eps = (eps_out && form.stage_comps == 0) ? 1 : 0;
-  const size_t smem =
-      fwd_smem(kf, r.g, eps_out ? std::min(3, form.stage_comps) : 0, &fa.r.stage_floats);
+  const size_t smem = eps_out ? fwd_eps_output(fa, kf, r.g, std::min(3, form.stage_comps),
+                                                form.stage_comps)
+                              : fwd_smem(kf, r.g, 0, &fa.r.stage_floats);
   st = launch(eps_out ? "eps_fwd_vjp_stencil" : "eps_vjp_stencil", kf.fn, dim3((unsigned)blocks),
               smem, &fa, s, true);
   if (st != EPS_OK) return st;

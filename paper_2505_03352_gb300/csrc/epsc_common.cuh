@@ -100,6 +100,9 @@ struct FwdRegion {
   // [4][nx][ny] and the seeds kernel adds them up.
   double *S;
   float *epsc;
+  int eps_tma;                   // 1: eps_hat components leave the 128-byte-swizzled
+                                 //    staging by one 4-D tensor store each (nz = 32;
+                                 //    single-region kernel, its args carry the map)
 };
 
 // Seeds kernel: regions laid end to end in one column space.
@@ -148,6 +151,9 @@ template <int NW>
 struct FwdArgsN {
   FwdRegion r;
   int *err;
+  // eps_hat as a {nz, ny, nx, 3} float tensor, box {nz, TJ, TI, 1}, 128-byte
+  // swizzle (used when r.eps_tma is set)
+  CUtensorMap eps_map;
   float w[NW];
 };
 using FwdArgs = FwdArgsN<MAX_BOX * MAX_BOX>;
@@ -270,6 +276,24 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // shared memory read by earlier bulk stores of this thread may be reused
 __device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// ... all but the most recent N groups of them
+template <int N>
+__device__ __forceinline__ void bulk_wait_read_n() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+// 4-D tensor store of a shared-memory box at coordinates {x, y, z, w},
+// tracked by the calling thread's bulk async-group; elements outside the
+// tensor are not written.  The box's shared-memory layout is the map's
+// (dense, swizzled as the map says); x * element size a multiple of 16.
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, const void *ssrc, int x, int y,
+                                             int z, int w) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];\n" ::"l"(
+          map),
+      "r"(s), "r"(x), "r"(y), "r"(z), "r"(w)
+      : "memory");
 }
 // earlier bulk stores of this thread have completed
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }

@@ -56,16 +56,39 @@ __device__ __forceinline__ float plane_value(int comp, int k, int k0, int nk, fl
   return clad;
 }
 
+// Planes 4 k4 .. 4 k4 + 3 of one eps_hat component of a column: `vin` on
+// the value run [lo, hi], `vf` on the face planes kf0, kf1 (eps_zz), `out`
+// elsewhere.  Groups of four planes wholly inside the run or wholly outside
+// [flo, fhi] take one branch (uniform over a warp when k4 is); the rest
+// select per plane.
+__device__ __forceinline__ float4 eps_planes4(int k4, float vin, float vf, float out, int lo,
+                                              int hi, int flo, int fhi, int kf0, int kf1) {
+  const int k = 4 * k4;
+  if (k >= lo && k + 3 <= hi) return make_float4(vin, vin, vin, vin);
+  if (k + 3 < flo || k > fhi) return make_float4(out, out, out, out);
+  float t[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int kk = k + q;
+    const bool in = kk >= lo && kk <= hi;
+    const bool face = kk == kf0 || kk == kf1;
+    t[q] = in ? vin : (face ? vf : out);
+  }
+  return make_float4(t[0], t[1], t[2], t[3]);
+}
+
 template <int BC>
 __device__ __forceinline__ int bc_map_t(int x, int n) {
   return BC == EPS_BC_CLAMP ? clampi(x, 0, n - 1) : wrapi(x, n);
 }
 
 // One tile (rows i0 .., columns j0 ..) of one region `rg`; `a` supplies the
-// conic weights as compile-time-indexed kernel parameters.
+// conic weights as compile-time-indexed kernel parameters.  `eps_map` (the
+// single-region kernel's parameter, or null) is the tensor map of eps_hat
+// for the swizzled staging form (rg.eps_tma).
 template <int RP1, int BC, class Args>
 __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, const int i0,
-                                         const int j0) {
+                                         const int j0, const CUtensorMap *eps_map = nullptr) {
   using S = FwdSmem<RP1>;
   constexpr int R = S::R;
   constexpr int CB = S::CB;
@@ -311,6 +334,51 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
           }
         }
       }
+    } else if (eps_map && rg.eps_tma && g.nz == 32 && c_first == 0 && c_last == 2 &&
+               per_round >= 1) {
+      // Swizzled staging: each column's 32 planes are one 128-byte row of a
+      // 1024-byte-aligned buffer, its 16-byte chunk k4 at chunk k4 ^ (row &
+      // 7), the layout of the map's 128-byte swizzle.  The eight lanes of a
+      // quarter-warp then store to eight different bank groups; in a plain
+      // row-major buffer the 128-byte row pitch puts all 32 lanes' 16-byte
+      // stores on the same four banks (eight times the shared-memory
+      // wavefronts).  One tensor store per component writes the tile's
+      // TI x TJ x nz box (clipped at the region edge).  Components rotate
+      // through min(per_round, 3) buffers, one bulk group each.
+      float *sbuf = smem;   // the stencil buffers are dead from here on; the
+                            // launch leaves 1 KB of slack for the alignment
+      sbuf += ((1024u - ((unsigned)__cvta_generic_to_shared(smem) & 1023u)) & 1023u) >> 2;
+      const int nbuf = min(per_round, 3);
+      const int sw = cc & 7;   // row = cr * TJ + cc, TJ a multiple of 8
+      __syncthreads();
+      for (int comp = 0; comp <= 2; ++comp) {
+        float *buf = sbuf + (comp % nbuf) * comp_floats;
+        if (comp >= nbuf) {   // the store that read this buffer must be done reading
+          if (tid == 0) {
+            if (nbuf == 1) bulk_wait_read_n<0>();
+            else bulk_wait_read_n<1>();
+          }
+          __syncthreads();
+        }
+        if (cr < nvi && cc < nvj) {
+          const float vin = comp == 0 ? ex : comp == 1 ? ey : ezi;
+          const int zlen = comp == 2 ? g.nk - 1 : g.nk;   // planes k0+1 .. k0+zlen take vin
+          const int lo = g.k0 + 1, hi = g.k0 + zlen;
+          const int flo = comp == 2 ? g.k0 : lo, fhi = comp == 2 ? g.k0 + g.nk : hi;
+          const int kf0 = comp == 2 ? g.k0 : -8, kf1 = comp == 2 ? g.k0 + g.nk : -8;
+          float4 *row = reinterpret_cast<float4 *>(buf + (cr * TJ + cc) * 32);
+#pragma unroll
+          for (int k4 = 0; k4 < 8; ++k4)
+            row[k4 ^ sw] = eps_planes4(k4, vin, ezf3, g.eps_clad, lo, hi, flo, fhi, kf0, kf1);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          tma_store_4d(eps_map, buf, 0, j0, i0, comp);
+          bulk_commit();
+        }
+      }
+      bulk_pending = true;
     } else if ((g.nz & 3) == 0 && per_round >= 1) {
       float *sbuf = smem;   // the stencil buffers are dead from here on
       const int nz4 = g.nz >> 2;
@@ -349,26 +417,8 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
             // the value run, all outside it, or mixed (per-plane selects).
             const int lo = g.k0 + 1, hi = g.k0 + zlen;       // value run [lo, hi]
             const int flo = comp == 2 ? g.k0 : lo, fhi = comp == 2 ? g.k0 + g.nk : hi;
-            const float4 vin4 = make_float4(vin, vin, vin, vin);
-            const float4 out4 = make_float4(out, out, out, out);
-            for (int k4 = 0; k4 < nz4; ++k4) {
-              const int k = 4 * k4;
-              if (k >= lo && k + 3 <= hi) {
-                dst[k4] = vin4;
-              } else if (k + 3 < flo || k > fhi) {
-                dst[k4] = out4;
-              } else {
-                float t[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  const int kk = k + q;
-                  const bool in = kk >= lo && kk <= hi;
-                  const bool face = kk == kf0 || kk == kf1;
-                  t[q] = in ? vin : (face ? ezf3 : out);
-                }
-                dst[k4] = make_float4(t[0], t[1], t[2], t[3]);
-              }
-            }
+            for (int k4 = 0; k4 < nz4; ++k4)
+              dst[k4] = eps_planes4(k4, vin, ezf3, out, lo, hi, flo, fhi, kf0, kf1);
           }
         }
         fence_proxy_async_smem();
@@ -492,7 +542,7 @@ __global__ void __launch_bounds__(NTHREADS, (RP1 <= 8 ? 4 : 3)) fwd_kernel(const
   const int ntiles = tiles_j * ((g.nx + TI - 1) / TI);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int ti = t / tiles_j;
-    fwd_tile<RP1, BC>(a, a.r, ti * TI, (t - ti * tiles_j) * TJ);
+    fwd_tile<RP1, BC>(a, a.r, ti * TI, (t - ti * tiles_j) * TJ, &a.eps_map);
     __syncthreads();   // the next tile reuses shared memory (bulk stores have read it)
   }
 }
