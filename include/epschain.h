@@ -148,6 +148,17 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps,
  *   ws, ws_bytes  device workspace of at least eps_workspace_size() bytes
  * The filtered density and projection are recomputed from C; nothing from
  * an earlier eps_forward is reused.
+ * Streams: all work is ordered on `stream` as one operation.  Problems of
+ * more than one wave of stencil tiles with the edge-replicate rule and
+ * complex64 fields run as a band pipeline: the field contraction streams
+ * the columns band by band on `stream`, and a library-owned stream of the
+ * current device (created with its events on first use, kept for the
+ * process, no device memory) runs the stencil, each band's seeds and the
+ * finished rows' scatter alongside; it is forked from `stream` by an event
+ * at the start of the call and joined back before the call's last
+ * operation, so work queued on `stream` after the call (and graph capture
+ * of `stream`) sees a completed call.  Calls from several host threads
+ * share that stream, so their pipelined parts run one after another.
  */
 eps_status_t eps_vjp(const eps_problem_t *prob, const float *C, int32_t n_lambda,
                      int32_t field_type, const void *const *EF, const void *const *EA,
@@ -523,7 +534,10 @@ eps_status_t eps_set_l2_fetch_granularity(int32_t bytes, int32_t *previous);
 
 /*
  * Per-kernel timing.  While enabled, each launch made by this library is
- * bracketed by CUDA events on its stream.  eps_profile_stop() waits for the
+ * bracketed by CUDA events on its stream, and the kernels of a call run one
+ * after another on the caller's stream (no programmatic dependent launch,
+ * no band pipeline), so each record is the kernel's own duration; calls are
+ * slower than unprofiled ones.  eps_profile_stop() waits for the
  * recorded events and fills up to max_entries records (kernel name, number
  * of launches, summed milliseconds); *n_entries gets the number written.
  * Host-side state is process-global: do not profile from several host

@@ -340,19 +340,17 @@ void support_window(const Geometry &g, int *x0, int *bx) {
   *bx = hi - lo;
 }
 
-// Contraction through bulk tensor copies; returns EPS_ERR_UNSUPPORTED when
-// the fields or the window do not fit its requirements (caller falls back).
-eps_status_t run_contract_tma(const Geometry &g, int n_lambda, const void *const *EF,
-                              const void *const *EA, const float (*fs)[3], float *Wm, int *err,
-                              cudaStream_t s) {
+// Arguments of the contraction through bulk tensor copies (every column);
+// EPS_ERR_UNSUPPORTED when the fields or the window do not fit its
+// requirements (the caller falls back).
+eps_status_t prepare_contract_tma(const Geometry &g, int n_lambda, const void *const *EF,
+                                  const void *const *EA, const float (*fs)[3], float *Wm,
+                                  int *err, ContractTmaArgs *ta) {
   PFN_encodeTiled enc = encode_tiled();
-  if (!enc) return EPS_ERR_UNSUPPORTED;
+  if (!enc || n_lambda < 1) return EPS_ERR_UNSUPPORTED;
   int x0 = 0, bx = 0;
   support_window(g, &x0, &bx);
   if (bx > TMA_BX_MAX || (g.nz & 1)) return EPS_ERR_UNSUPPORTED;
-  static_assert(sizeof(ContractTmaArgs) < 8192, "kernel parameter space");
-  ContractTmaArgs targs;
-  ContractTmaArgs *ta = &targs;
   std::memset(ta, 0, sizeof(*ta));
   const long ncol = (long)g.nx * g.ny;
   const size_t comp_bytes = (size_t)ncol * g.nz * 8;
@@ -380,16 +378,37 @@ eps_status_t run_contract_tma(const Geometry &g, int n_lambda, const void *const
   ta->nlambda = n_lambda;
   ta->x0 = x0;
   ta->bx = bx;
+  ta->col_lo = 0;
+  ta->col_hi = ncol;
+  return EPS_OK;
+}
+
+// One launch of the prepared contraction over the columns [col_lo, col_hi).
+eps_status_t launch_contract_tma(ContractTmaArgs *ta, long col_lo, long col_hi,
+                                 cudaStream_t s) {
+  static_assert(sizeof(ContractTmaArgs) < 8192, "kernel parameter space");
   int nsm = 0;
   eps_status_t st = sm_count(&nsm);
-  if (st == EPS_OK) {
-    const long nchunks = (ncol + TMA_BY - 1) / TMA_BY;
-    const long blocks = std::max<long>(1, std::min<long>(nchunks, (long)nsm * CONTRACT_BLOCKS_PER_SM));
-    const size_t smem = (size_t)TMA_NSTAGE * 6 * TMA_BY * bx * 4 + 128;
-    st = launch("eps_vjp_contract", contract_tma_entry(n_lambda), dim3((unsigned)blocks), smem, ta,
-                s);
-  }
-  return st;
+  if (st != EPS_OK) return st;
+  ta->col_lo = col_lo;
+  ta->col_hi = col_hi;
+  const long nchunks = (col_hi - col_lo + TMA_BY - 1) / TMA_BY;
+  if (nchunks <= 0) return EPS_OK;
+  const long blocks = std::max<long>(1, std::min<long>(nchunks, (long)nsm * CONTRACT_BLOCKS_PER_SM));
+  const size_t smem = (size_t)TMA_NSTAGE * 6 * TMA_BY * ta->bx * 4 + 128;
+  return launch("eps_vjp_contract", contract_tma_entry(ta->nlambda), dim3((unsigned)blocks), smem,
+                ta, s);
+}
+
+// Contraction through bulk tensor copies over every column;
+// EPS_ERR_UNSUPPORTED as prepare_contract_tma.
+eps_status_t run_contract_tma(const Geometry &g, int n_lambda, const void *const *EF,
+                              const void *const *EA, const float (*fs)[3], float *Wm, int *err,
+                              cudaStream_t s) {
+  ContractTmaArgs targs;
+  const eps_status_t st = prepare_contract_tma(g, n_lambda, EF, EA, fs, Wm, err, &targs);
+  if (st != EPS_OK) return st;
+  return launch_contract_tma(&targs, 0, (long)g.nx * g.ny, s);
 }
 
 // Arguments of the batched TMA contraction over the regions of `ca`
@@ -499,43 +518,67 @@ size_t packed_bytes(const Geometry &g) {
   return 16 + (size_t)3 * g.nx * g.ny * packed_planes(g) * 4;
 }
 
+// Arguments of the packed contraction; *bulk is set when every field
+// buffer suits the bulk-copy kernel (16-byte aligned), which alone takes a
+// column range (launch_contract_packed).
+eps_status_t prepare_contract_packed(const Geometry &g, int n_lambda, int type,
+                                     const void *const *EF, const void *const *EA,
+                                     const float (*fs)[3], float *Wm, int *err,
+                                     ContractPackedArgs *pa, bool *bulk) {
+  std::memset(pa, 0, sizeof(*pa));
+  pa->nx = g.nx;
+  pa->ny = g.ny;
+  pa->k0 = g.k0;
+  pa->nk = g.nk;
+  pa->np = packed_planes(g);
+  pa->nlambda = n_lambda;
+  pa->type = type;
+  for (int l = 0; l < n_lambda; ++l) {
+    pa->EF[l] = (const unsigned char *)EF[l];
+    pa->EA[l] = (const unsigned char *)EA[l];
+    for (int c = 0; c < 3; ++c) pa->fs[l][c] = fs[l][c];
+  }
+  pa->W = Wm;
+  pa->err = err;
+  pa->col_lo = 0;
+  pa->col_hi = (long)g.nx * g.ny;
+  *bulk = n_lambda > 0;
+  for (int l = 0; l < n_lambda; ++l) *bulk = *bulk && aligned(EF[l], 16) && aligned(EA[l], 16);
+  return EPS_OK;
+}
+
+// The bulk-copy packed contraction over the columns [col_lo, col_hi): a ring
+// of PACKED_NSTAGE stages of 6 x PK_BY x 4 np bytes (37 KB at nk = 11) in
+// PACKED_BLOCKS_PER_SM blocks per SM, about 74 KB per block, so stencil
+// blocks (32 KB with one eps_hat component staged per round) still fit
+// beside the two.
+eps_status_t launch_contract_packed(ContractPackedArgs *pa, long col_lo, long col_hi,
+                                    cudaStream_t s) {
+  int nsm = 0;
+  eps_status_t st = sm_count(&nsm);
+  if (st != EPS_OK) return st;
+  pa->nstage = PACKED_NSTAGE;
+  pa->col_lo = col_lo;
+  pa->col_hi = col_hi;
+  const size_t smem = (size_t)PACKED_NSTAGE * 6 * PK_BY * pa->np * 4 + 128;
+  const long nchunks = (col_hi - col_lo + PK_BY - 1) / PK_BY;
+  if (nchunks <= 0) return EPS_OK;
+  const long blocks = std::max<long>(1, std::min<long>(nchunks, (long)nsm * PACKED_BLOCKS_PER_SM));
+  return launch("eps_vjp_contract_packed", contract_packed_bulk_entry(), dim3((unsigned)blocks),
+                smem, pa, s, false, PK_THREADS);
+}
+
 eps_status_t run_contract_packed(const Geometry &g, int n_lambda, int type, const void *const *EF,
                                  const void *const *EA, const float (*fs)[3], float *Wm, int *err,
                                  cudaStream_t s) {
   ContractPackedArgs pa;
-  std::memset(&pa, 0, sizeof(pa));
-  pa.nx = g.nx;
-  pa.ny = g.ny;
-  pa.k0 = g.k0;
-  pa.nk = g.nk;
-  pa.np = packed_planes(g);
-  pa.nlambda = n_lambda;
-  pa.type = type;
-  for (int l = 0; l < n_lambda; ++l) {
-    pa.EF[l] = (const unsigned char *)EF[l];
-    pa.EA[l] = (const unsigned char *)EA[l];
-    for (int c = 0; c < 3; ++c) pa.fs[l][c] = fs[l][c];
-  }
-  pa.W = Wm;
-  pa.err = err;
-  int nsm = 0;
-  eps_status_t st = sm_count(&nsm);
+  bool bulk = false;
+  eps_status_t st = prepare_contract_packed(g, n_lambda, type, EF, EA, fs, Wm, err, &pa, &bulk);
   if (st != EPS_OK) return st;
   const long ncol = (long)g.nx * g.ny;
-  bool bulk = true;
-  for (int l = 0; l < n_lambda; ++l) bulk = bulk && aligned(EF[l], 16) && aligned(EA[l], 16);
-  if (bulk && n_lambda > 0) {
-    // ring of PACKED_NSTAGE stages of 6 x PK_BY x 4 np bytes (37 KB at nk =
-    // 11) in PACKED_BLOCKS_PER_SM blocks per SM: about 74 KB per block, so
-    // stencil blocks (32 KB with one eps_hat component staged per round)
-    // still fit beside the two
-    pa.nstage = PACKED_NSTAGE;
-    const size_t smem = (size_t)PACKED_NSTAGE * 6 * PK_BY * pa.np * 4 + 128;
-    const long nchunks = (ncol + PK_BY - 1) / PK_BY;
-    const long blocks = std::max<long>(1, std::min<long>(nchunks, (long)nsm * PACKED_BLOCKS_PER_SM));
-    return launch("eps_vjp_contract_packed", contract_packed_bulk_entry(), dim3((unsigned)blocks),
-                  smem, &pa, s, false, PK_THREADS);
-  }
+  if (bulk) return launch_contract_packed(&pa, 0, ncol, s);
+  int nsm = 0;
+  if ((st = sm_count(&nsm)) != EPS_OK) return st;
   const long blocks = std::max<long>(1, std::min<long>((ncol + NTHREADS - 1) / NTHREADS, (long)nsm * 8));
   return launch("eps_vjp_contract_packed", contract_packed_entry(), dim3((unsigned)blocks), 0, &pa, s);
 }
@@ -549,7 +592,11 @@ eps_status_t run_seeds(const SeedsArgs &sa, cudaStream_t s) {
   if (sa.ncol == 0) return EPS_OK;
   // one thread per column, or per four columns for one region of whole float4
   // rows (a full-occupancy elementwise pass), capped for very large calls
-  const long items = (sa.n == 1 && (sa.r[0].ncol & 3) == 0) ? sa.ncol / 4 : sa.ncol;
+  const long cols = sa.band_hi > 0 ? sa.band_hi - sa.band_lo : sa.ncol;
+  if (cols <= 0) return EPS_OK;
+  const bool vec = sa.n == 1 && (sa.r[0].ncol & 3) == 0 && (sa.band_lo & 3) == 0 &&
+                   (sa.band_hi & 3) == 0;
+  const long items = vec ? (cols + 3) / 4 : cols;
   const long blocks = std::max<long>(1, std::min<long>((items + NTHREADS - 1) / NTHREADS, (long)nsm * 64));
   return launch("eps_vjp_seeds", seeds_entry(), dim3((unsigned)blocks), 0, (void *)&sa, s, false);
 }
@@ -587,12 +634,16 @@ eps_status_t stencil_form(const Geometry &g, StencilForm *f, long *blocks) {
   return EPS_OK;
 }
 
+// (band_hi > 0: only the columns [band_lo, band_hi))
 eps_status_t run_seeds_one(const Geometry &g, const float *W, float *seeds, int *err,
-                           cudaStream_t s, const float *epsc = nullptr, double *S = nullptr) {
+                           cudaStream_t s, const float *epsc = nullptr, double *S = nullptr,
+                           long band_lo = 0, long band_hi = 0) {
   SeedsArgs sa;
   std::memset(&sa, 0, sizeof(sa));
   sa.n = 1;
   sa.ncol = (long)g.nx * g.ny;
+  sa.band_lo = band_lo;
+  sa.band_hi = band_hi;
   sa.r[0] = SeedsRegion{0, sa.ncol, W, seeds};
   sa.err = err;
   sa.epsc = epsc;
@@ -661,18 +712,24 @@ bool scatter_maps(const Resolved &r, const float *seeds, const float *pd4, const
   return true;
 }
 
+// The scatter over the tile rows [t0, t1) (t1 < 0: to the last row), launched
+// with programmatic dependent launch behind the kernel queued ahead of it
+// when `pdl`.
 eps_status_t run_scatter(const Resolved &r, const float *seeds, const float *pd4, const float *ie2,
-                         float *dJdC,
-                         int *err, cudaStream_t s) {
-  // Bulk-copy staging pays from two waves of tiles up.  Within one wave every
-  // block stages at once, and the element-wise copies of all its threads
-  // deliver a block's inputs as soon (cfg3: 541 us against 552 us for the
-  // call; cfg2 unchanged).
+                         float *dJdC, int *err, cudaStream_t s, int t0 = 0, int t1 = -1,
+                         bool pdl = true) {
+  // Bulk-copy staging pays from two waves of tiles up (of the whole grid).
+  // Within one wave every block stages at once, and the element-wise copies
+  // of all its threads deliver a block's inputs as soon (cfg3: 541 us
+  // against 552 us for the call; cfg2 unchanged).
   int nsm = 0;
   eps_status_t st = sm_count(&nsm);
   if (st != EPS_OK) return st;
-  const dim3 grid = bwd_grid(r.g);
-  if ((long)grid.x * grid.y > (long)ONE_WAVE_TILES_PER_SM * nsm) {
+  const dim3 full = bwd_grid(r.g);
+  if (t1 < 0 || t1 > (int)full.y) t1 = (int)full.y;
+  if (t0 >= t1) return EPS_OK;
+  const dim3 grid(full.x, (unsigned)(t1 - t0));
+  if ((long)full.x * full.y > (long)ONE_WAVE_TILES_PER_SM * nsm) {
     const KernelEntry kt = bwd_tma_entry(r.rp1, r.g.bc);
     BwdTmaArgs ta;
     std::memset(&ta, 0, sizeof(ta));
@@ -683,8 +740,9 @@ eps_status_t run_scatter(const Resolved &r, const float *seeds, const float *pd4
       ta.r.ie2 = ie2;
       ta.r.dJdC = dJdC;
       ta.err = err;
+      ta.ty0 = t0;
       std::memcpy(ta.w, r.w, sizeof(ta.w));
-      return launch("eps_vjp_scatter", kt.fn, grid, kt.smem, &ta, s, true);
+      return launch("eps_vjp_scatter", kt.fn, grid, kt.smem, &ta, s, pdl);
     }
   }
   BwdArgs ba;
@@ -695,9 +753,10 @@ eps_status_t run_scatter(const Resolved &r, const float *seeds, const float *pd4
   ba.r.ie2 = ie2;
   ba.r.dJdC = dJdC;
   ba.err = err;
+  ba.ty0 = t0;
   std::memcpy(ba.w, r.w, sizeof(ba.w));
   const KernelEntry k = bwd_entry(r.rp1, r.g.bc);
-  return launch("eps_vjp_scatter", k.fn, grid, k.smem, &ba, s, true);
+  return launch("eps_vjp_scatter", k.fn, grid, k.smem, &ba, s, pdl);
 }
 
 }  // namespace
@@ -768,6 +827,70 @@ eps_status_t eps_forward(const eps_problem_t *prob, const float *C, float *eps, 
 
 namespace {
 
+// Auxiliary streams of the concurrent grouped form: one set per device,
+// created on first use and kept for the process.  A call forks them from the
+// caller's stream with an event and joins them back before it returns, so
+// ordering against other work on the caller's stream (and graph capture of
+// that stream) is kept; the mutex makes the enqueue sequences of calls from
+// different host threads, which share the set, follow one another.
+// The set also holds the stream and events of the single-region band
+// pipeline (vjp_pipelined).
+constexpr int AUX_STREAMS = 8;
+constexpr int MAX_PIPE_BANDS = 16;
+struct AuxSet {
+  bool ready = false;
+  cudaStream_t st[AUX_STREAMS];
+  cudaEvent_t fork, mid, join[AUX_STREAMS], join2[AUX_STREAMS];
+  cudaStream_t pipe;
+  cudaEvent_t pipe_fork, pipe_join, band[MAX_PIPE_BANDS];
+};
+std::mutex g_aux_mu;
+AuxSet g_aux[64];
+
+eps_status_t aux_set(AuxSet **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return EPS_ERR_CUDA;
+  AuxSet &a = g_aux[dev];
+  if (!a.ready) {
+    for (int i = 0; i < AUX_STREAMS; ++i) {
+      if (cudaStreamCreateWithFlags(&a.st[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&a.join[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&a.join2[i], cudaEventDisableTiming) != cudaSuccess)
+        return EPS_ERR_CUDA;
+    }
+    if (cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.mid, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&a.pipe, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.pipe_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.pipe_join, cudaEventDisableTiming) != cudaSuccess)
+      return EPS_ERR_CUDA;
+    for (int i = 0; i < MAX_PIPE_BANDS; ++i)
+      if (cudaEventCreateWithFlags(&a.band[i], cudaEventDisableTiming) != cudaSuccess)
+        return EPS_ERR_CUDA;
+    a.ready = true;
+  }
+  *out = &a;
+  return EPS_OK;
+}
+
+// Every stream in `waiters` waits for the work enqueued so far on `s`.
+eps_status_t fork_streams(cudaStream_t s, cudaEvent_t ev, const cudaStream_t *waiters, int n) {
+  if (cudaEventRecord(ev, s) != cudaSuccess) return EPS_ERR_CUDA;
+  for (int i = 0; i < n; ++i)
+    if (cudaStreamWaitEvent(waiters[i], ev, 0) != cudaSuccess) return EPS_ERR_CUDA;
+  return EPS_OK;
+}
+
+// `s` waits for the work enqueued so far on every stream in `workers`.
+eps_status_t join_streams(cudaStream_t s, const cudaEvent_t *evs, const cudaStream_t *workers,
+                          int n) {
+  for (int i = 0; i < n; ++i) {
+    if (cudaEventRecord(evs[i], workers[i]) != cudaSuccess) return EPS_ERR_CUDA;
+    if (cudaStreamWaitEvent(s, evs[i], 0) != cudaSuccess) return EPS_ERR_CUDA;
+  }
+  return EPS_OK;
+}
+
 // Argument checks of eps_vjp (everything but the problem itself, which
 // `r` already resolved); *skip is set for an empty problem.
 eps_status_t vjp_args(const Resolved &r, const float *C, int32_t n_lambda, int32_t field_type,
@@ -805,6 +928,111 @@ eps_status_t vjp_args(const Resolved &r, const float *C, int32_t n_lambda, int32
 
 namespace {
 
+// Band pipeline of a multi-wave single-region call (edge-replicate rule,
+// complex64 fields through the bulk-copy contraction).  The contraction
+// runs band by band (consecutive column ranges) on the caller's stream; a
+// pipeline stream runs the stencil alongside, then, as each band's column
+// sums complete, that band's seeds and the scatter of every tile row whose
+// seed maps are complete.  All but the last band's seeds and scatter then
+// overlap the field stream instead of following it.
+//
+// Measured on a GB300 (L2 flushed, one box, medians; 0 bands = the
+// single-stream order):
+//   bands                     0      3      4      5      6      8
+//   3000 x 3000, 8 lambda  2427   2373   2371   2364   2367   2345-2347 (another box: 0 -> 2415)
+//   2000 x 2000, 3 lambda   516    501    514    524    533    561
+// Each band boundary costs a contraction tail and ramp, and queued stencil
+// or scatter blocks take the slots the next band's blocks would get; the
+// shorter three-wavelength stream pays for that first.  Tried and not
+// kept: the contraction bands on a stream of the highest priority (2494 us
+// at 4 bands), the stencil as a persistent grid of two blocks per SM
+// (2377 / 508 us at 4 bands).
+constexpr int PIPE_BANDS = 3;
+// (packed fields take the pipeline too once measured; off until then)
+constexpr bool PIPE_PACKED = false;
+static_assert(PIPE_BANDS <= MAX_PIPE_BANDS, "band events");
+
+// Highest Yee row of the seed maps that scatter tile row t reads, its
+// bulk-copy boxes included (edge-replicate rule: no wrap).
+int scatter_seed_row_hi(const Resolved &r, int t) {
+  const int R = r.rp1 - 1;
+  const int ga_lo = TA * t - (t == 0 ? R : 0);   // the fold halo of the first row
+  const int da_lo = ga_lo - R;
+  const int ci_lo = da_lo >= 0 ? da_lo / 2 : -((1 - da_lo) / 2);   // floor(da_lo / 2)
+  return ci_lo + scatter_boxes(r.rp1).nci;
+}
+
+struct PipeCall {
+  const Resolved *r;
+  ContractTmaArgs *ta;          // prepared contraction (every column): complex64 fields,
+  ContractPackedArgs *pa;       // or packed fields (bulk-copy kernel); one is null
+  FwdArgs *fa;                  // stencil arguments (seed factors: defer form)
+  KernelEntry kf;
+  size_t fsmem;
+  long fblocks;
+  const char *fname;
+  float *W, *seeds, *pd4, *ie2, *dJdC, *epsc;
+  double *S;
+  int *err;
+};
+
+eps_status_t vjp_pipelined(const PipeCall &c, cudaStream_t s) {
+  const Resolved &r = *c.r;
+  const Geometry &g = r.g;
+  int nsm = 0;
+  eps_status_t st = sm_count(&nsm);
+  if (st != EPS_OK) return st;
+  std::lock_guard<std::mutex> lk(g_aux_mu);
+  AuxSet *aux = nullptr;
+  if ((st = aux_set(&aux)) != EPS_OK) return st;
+  // Bands of whole rounds of the contraction grid (one chunk per block and
+  // round), so every block of a band has the same number of chunks.
+  const long ncol = (long)g.nx * g.ny;
+  const long chunk_cols = c.ta ? TMA_BY : PK_BY;
+  const long nchunks = (ncol + chunk_cols - 1) / chunk_cols;
+  const long per_round = (long)nsm * (c.ta ? CONTRACT_BLOCKS_PER_SM : PACKED_BLOCKS_PER_SM);
+  const long rounds = (nchunks + per_round - 1) / per_round;
+  const int nb = (int)std::max<long>(1, std::min<long>(PIPE_BANDS, rounds));
+  const int T = (int)bwd_grid(g).y;
+
+  if (cudaEventRecord(aux->pipe_fork, s) != cudaSuccess ||
+      cudaStreamWaitEvent(aux->pipe, aux->pipe_fork, 0) != cudaSuccess)
+    return EPS_ERR_CUDA;
+  int t_done = 0;
+  for (int b = 0; b < nb; ++b) {
+    const long lo = std::min(ncol, rounds * b / nb * per_round * chunk_cols);
+    const long hi =
+        b == nb - 1 ? ncol : std::min(ncol, rounds * (b + 1) / nb * per_round * chunk_cols);
+    st = c.ta ? launch_contract_tma(c.ta, lo, hi, s) : launch_contract_packed(c.pa, lo, hi, s);
+    if (st != EPS_OK) return st;
+    if (cudaEventRecord(aux->band[b], s) != cudaSuccess) return EPS_ERR_CUDA;
+    if (b == 0 && (st = launch(c.fname, c.kf.fn, dim3((unsigned)c.fblocks), c.fsmem, c.fa,
+                               aux->pipe, false)) != EPS_OK)
+      return st;
+    if (cudaStreamWaitEvent(aux->pipe, aux->band[b], 0) != cudaSuccess) return EPS_ERR_CUDA;
+    if ((st = run_seeds_one(g, c.W, c.seeds, c.err, aux->pipe, c.S ? c.epsc : nullptr, c.S, lo,
+                            hi)) != EPS_OK)
+      return st;
+    // tile rows whose seed rows (all below the first incomplete Yee row) are done
+    int t_ready = T;
+    if (b < nb - 1) {
+      const long rows_done = hi / g.ny;
+      t_ready = t_done;
+      while (t_ready < T && scatter_seed_row_hi(r, t_ready) < rows_done) ++t_ready;
+    }
+    if (t_ready > t_done) {
+      if ((st = run_scatter(r, c.seeds, c.pd4, c.ie2, c.dJdC, c.err, aux->pipe, t_done, t_ready,
+                            false)) != EPS_OK)
+        return st;
+      t_done = t_ready;
+    }
+  }
+  if (cudaEventRecord(aux->pipe_join, aux->pipe) != cudaSuccess ||
+      cudaStreamWaitEvent(s, aux->pipe_join, 0) != cudaSuccess)
+    return EPS_ERR_CUDA;
+  return EPS_OK;
+}
+
 // The fused forward + Eq. 1 VJP of eps_vjp; with S non-null also the
 // surrogate S = sum over the J-support voxels of eps_hat * w (zeroed here,
 // accumulated by the stencil or the seeds kernel).
@@ -831,7 +1059,7 @@ eps_status_t vjp_fused(const eps_problem_t *prob, const float *C, int32_t n_lamb
   float *ie2 = (float *)((char *)ws + L.ie2);
   float *epsc = (float *)((char *)ws + L.epsc);
 
-  // 1. Eq. 1 column sums (streaming over the J-support planes)
+  // Eq. 1 column sums: per-wavelength scales of the components
   ContractArgs ca;
   std::memset(&ca, 0, sizeof(ca));
   ca.nx = r.g.nx;
@@ -854,16 +1082,8 @@ eps_status_t vjp_fused(const eps_problem_t *prob, const float *C, int32_t n_lamb
       ca.fs[l][c] = sc;
     }
   }
-  if (field_type == EPS_FIELD_C64) {
-    st = (n_lambda > 0) ? run_contract_tma(r.g, n_lambda, EF, EA, ca.fs, Wm, err, s)
-                        : EPS_ERR_UNSUPPORTED;
-    if (st == EPS_ERR_UNSUPPORTED) st = run_contract(ca, sector_ok ? 4 : 8, s);
-  } else {
-    st = run_contract_packed(r.g, n_lambda, field_type, EF, EA, ca.fs, Wm, err, s);
-  }
-  if (st != EPS_OK) return st;
 
-  // 2. forward chain + seeds (overlaps the contraction until it needs W)
+  // forward chain + seeds (overlaps the contraction until it needs W)
   FwdArgs fa;
   fill_fwd_common(fa, r, C, err);
   fa.r.mode = MODE_C64;
@@ -885,8 +1105,49 @@ eps_status_t vjp_fused(const eps_problem_t *prob, const float *C, int32_t n_lamb
   const size_t smem = eps_out ? fwd_eps_output(fa, kf, r.g, std::min(3, form.stage_comps),
                                                 form.stage_comps)
                               : fwd_smem(kf, r.g, 0, &fa.r.stage_floats);
-  st = launch(eps_out ? "eps_fwd_vjp_stencil" : "eps_vjp_stencil", kf.fn, dim3((unsigned)blocks),
-              smem, &fa, s, true);
+  const char *fname = eps_out ? "eps_fwd_vjp_stencil" : "eps_vjp_stencil";
+
+  // (profiling runs the kernels one after another, so each event pair
+  // times one kernel alone)
+  bool prof = false;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof = g_prof_on;
+  }
+  if (PIPE_BANDS > 1 && !prof && n_lambda > 0 && form.defer == 1 && r.g.bc == EPS_BC_CLAMP) {
+    if (field_type == EPS_FIELD_C64) {
+      std::unique_ptr<ContractTmaArgs> ta(new ContractTmaArgs);
+      st = prepare_contract_tma(r.g, n_lambda, EF, EA, ca.fs, Wm, err, ta.get());
+      if (st == EPS_OK) {
+        PipeCall pc{&r, ta.get(), nullptr, &fa, kf, smem, blocks, fname, Wm, seeds, pd4, ie2,
+                    dJdC, epsc, S, err};
+        return vjp_pipelined(pc, s);
+      }
+      if (st != EPS_ERR_UNSUPPORTED) return st;
+    } else if (PIPE_PACKED) {
+      ContractPackedArgs pa;
+      bool bulk = false;
+      st = prepare_contract_packed(r.g, n_lambda, field_type, EF, EA, ca.fs, Wm, err, &pa, &bulk);
+      if (st != EPS_OK) return st;
+      if (bulk) {
+        PipeCall pc{&r, nullptr, &pa, &fa, kf, smem, blocks, fname, Wm, seeds, pd4, ie2, dJdC,
+                    epsc, S, err};
+        return vjp_pipelined(pc, s);
+      }
+    }
+  }
+
+  // 1. Eq. 1 column sums (streaming over the J-support planes)
+  if (field_type == EPS_FIELD_C64) {
+    st = (n_lambda > 0) ? run_contract_tma(r.g, n_lambda, EF, EA, ca.fs, Wm, err, s)
+                        : EPS_ERR_UNSUPPORTED;
+    if (st == EPS_ERR_UNSUPPORTED) st = run_contract(ca, sector_ok ? 4 : 8, s);
+  } else {
+    st = run_contract_packed(r.g, n_lambda, field_type, EF, EA, ca.fs, Wm, err, s);
+  }
+  if (st != EPS_OK) return st;
+  // 2. the stencil, with programmatic dependent launch behind the contraction
+  st = launch(fname, kf.fn, dim3((unsigned)blocks), smem, &fa, s, true);
   if (st != EPS_OK) return st;
   // 3. (seeds-kernel form) seeds = factor * W, once both grids are done
   if (form.defer == 1 &&
@@ -1458,59 +1719,6 @@ eps_status_t run_bwd_batch(const std::vector<Resolved> &rs, const eps_problem_t 
                            cudaStream_t s) {
   if (t.multi) return run_bwd_multi(make_sets(rs, probs), rs, regions, t.bwd_bps, err, s);
   return run_bwd_grouped(make_groups(rs, probs), rs, regions, t.bwd_bulk, t.bwd_cols, err, s);
-}
-
-// Auxiliary streams of the concurrent grouped form: one set per device,
-// created on first use and kept for the process.  A call forks them from the
-// caller's stream with an event and joins them back before it returns, so
-// ordering against other work on the caller's stream (and graph capture of
-// that stream) is kept; the mutex makes the enqueue sequences of calls from
-// different host threads, which share the set, follow one another.
-constexpr int AUX_STREAMS = 8;
-struct AuxSet {
-  bool ready = false;
-  cudaStream_t st[AUX_STREAMS];
-  cudaEvent_t fork, mid, join[AUX_STREAMS], join2[AUX_STREAMS];
-};
-std::mutex g_aux_mu;
-AuxSet g_aux[64];
-
-eps_status_t aux_set(AuxSet **out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return EPS_ERR_CUDA;
-  AuxSet &a = g_aux[dev];
-  if (!a.ready) {
-    for (int i = 0; i < AUX_STREAMS; ++i) {
-      if (cudaStreamCreateWithFlags(&a.st[i], cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&a.join[i], cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&a.join2[i], cudaEventDisableTiming) != cudaSuccess)
-        return EPS_ERR_CUDA;
-    }
-    if (cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&a.mid, cudaEventDisableTiming) != cudaSuccess)
-      return EPS_ERR_CUDA;
-    a.ready = true;
-  }
-  *out = &a;
-  return EPS_OK;
-}
-
-// Every stream in `waiters` waits for the work enqueued so far on `s`.
-eps_status_t fork_streams(cudaStream_t s, cudaEvent_t ev, const cudaStream_t *waiters, int n) {
-  if (cudaEventRecord(ev, s) != cudaSuccess) return EPS_ERR_CUDA;
-  for (int i = 0; i < n; ++i)
-    if (cudaStreamWaitEvent(waiters[i], ev, 0) != cudaSuccess) return EPS_ERR_CUDA;
-  return EPS_OK;
-}
-
-// `s` waits for the work enqueued so far on every stream in `workers`.
-eps_status_t join_streams(cudaStream_t s, const cudaEvent_t *evs, const cudaStream_t *workers,
-                          int n) {
-  for (int i = 0; i < n; ++i) {
-    if (cudaEventRecord(evs[i], workers[i]) != cudaSuccess) return EPS_ERR_CUDA;
-    if (cudaStreamWaitEvent(s, evs[i], 0) != cudaSuccess) return EPS_ERR_CUDA;
-  }
-  return EPS_OK;
 }
 
 eps_status_t vjp_batched_impl(int32_t n, const eps_problem_t *probs, const float *const *C,

@@ -282,17 +282,37 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
   sG += shg;
 
   // ---- Sobel^T: dU_c at the touched cells ----------------------------------
-  // interior cells use the plain transposed stencil; cells next to an edge
-  // replicate use the folded weights
+  // Cells whose three source rows and columns all exist and fold nothing
+  // (every cell under the wrap rule; 1 <= cell <= n - 2 under edge
+  // replicate) take the plain transposed stencil with its constant weights,
+  //   d/dU of g_x: D(e) S(f),  of g_y: S(e) D(f),  D = (1, 0, -1), S = (1, 2, 1)
+  // over source offsets e (rows) and f (columns); cells next to an edge
+  // replicate use the folded weights.
   for (int c = tx; c < NCJ; c += 32) {
     const int vj = cj_lo + c;
     const bool col_real = vj >= 0 && vj < g.ny;
+    const bool col_plain = !clamp || (vj >= 1 && vj <= g.ny - 2);
     float wdy[3], wsy[3];
     sobel_t_weights(clamp ? vj : wrapi(vj, g.ny), g.ny, BC, wdy, wsy);
     for (int r = ty; r < NCI; r += 8) {
       const int vi = ci_lo + r;
       float ux = 0.f, uy = 0.f;
-      if (!clamp || (col_real && vi >= 0 && vi < g.nx)) {
+      if (col_plain && (!clamp || (vi >= 1 && vi <= g.nx - 2))) {
+        const float *a0 = sG + r * S::NGJ + c;   // source cell (vi - 1, vj - 1)
+        const float *a2 = a0 + 2 * S::NGJ;        // source row vi + 1
+        const float *b0 = a0 + S::NG;             // the g_y seeds of U_x
+        const float *b1 = b0 + S::NGJ;
+        const float *b2 = b0 + 2 * S::NGJ;
+        ux = ((a0[0] + 2.f * a0[1] + a0[2]) - (a2[0] + 2.f * a2[1] + a2[2])) +
+             ((b0[0] + 2.f * b1[0] + b2[0]) - (b0[2] + 2.f * b1[2] + b2[2]));
+        const float *c0 = a0 + 2 * S::NG;         // the g_x, g_y seeds of U_y
+        const float *c2 = c0 + 2 * S::NGJ;
+        const float *d0 = a0 + 3 * S::NG;
+        const float *d1 = d0 + S::NGJ;
+        const float *d2 = d0 + 2 * S::NGJ;
+        uy = ((c0[0] + 2.f * c0[1] + c0[2]) - (c2[0] + 2.f * c2[1] + c2[2])) +
+             ((d0[0] + 2.f * d1[0] + d2[0]) - (d0[2] + 2.f * d1[2] + d2[2]));
+      } else if (!clamp || (col_real && vi >= 0 && vi < g.nx)) {
         float wdx[3], wsx[3];
         sobel_t_weights(clamp ? vi : wrapi(vi, g.nx), g.nx, BC, wdx, wsx);
 #pragma unroll
@@ -386,13 +406,13 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
 
 template <int RP1, int BC>
 __global__ void __launch_bounds__(NTHREADS) bwd_kernel(const __grid_constant__ BwdArgsR<RP1> a) {
-  bwd_tile<RP1, BC>(a, a.r, blockIdx.y * TA, blockIdx.x * TB);
+  bwd_tile<RP1, BC>(a, a.r, (blockIdx.y + a.ty0) * TA, blockIdx.x * TB);
 }
 
 // The same scatter with bulk-copy staging of the interior tiles.
 template <int RP1, int BC>
 __global__ void __launch_bounds__(NTHREADS) bwd_tma_kernel(const __grid_constant__ BwdTmaArgsR<RP1> a) {
-  bwd_tile<RP1, BC, true>(a, a.r, blockIdx.y * TA, blockIdx.x * TB, &a.maps[0]);
+  bwd_tile<RP1, BC, true>(a, a.r, (blockIdx.y + a.ty0) * TA, blockIdx.x * TB, &a.maps[0]);
 }
 
 // Batched scatter of one radius group with bulk-copy staging: block b takes

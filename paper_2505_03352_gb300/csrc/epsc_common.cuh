@@ -115,6 +115,9 @@ struct SeedsRegion {
 struct SeedsArgs {
   int n;
   long ncol;
+  // single-region calls: only the columns [band_lo, band_hi) (one band of a
+  // pipelined call); band_hi == 0: every column
+  long band_lo, band_hi;
   int *err;                      // error flag (debug bounds checks)
   // Eq. 1 surrogate (single-region calls; null: not requested): *S +=
   // sum over columns of epsc . W, epsc [4][nx][ny] from the stencil
@@ -184,6 +187,7 @@ template <int NW>
 struct BwdArgsN {
   BwdRegion r;
   int *err;
+  int ty0;                       // first tile row of the launch (grid row 0)
   float w[NW];
 };
 
@@ -194,6 +198,7 @@ template <int NW>
 struct __align__(128) BwdTmaArgsN {
   BwdRegion r;
   int *err;
+  int ty0;                       // first tile row of the launch (grid row 0)
   // P' deps / 4 and 1 / eps^2 ({my, mx, 1}); the six mean seeds and the four
   // Sobel seeds ({ny, nx, NSEED}, one box each)
   CUtensorMap maps[4];
@@ -317,8 +322,11 @@ __device__ __forceinline__ void griddep_launch_dependents() {
 // R columns left of output 0; output k is
 //     sum_{p,q} w[(p+R)(2R+1) + q+R] * src[(k + p + R) * pitch + q + R].
 // Every input row is read once from shared memory and reused by all NA
-// outputs.  Each output adds the per-row partial sums of its taps: fewer
-// rounding steps in sequence than one long fma chain, which matters where a
+// outputs.  The cone is symmetric in q (w depends on p^2 + q^2 only, and the
+// host table is exactly symmetric), so each row first pairs the inputs at
+// +q and -q, and each output takes R + 1 taps per row instead of 2R + 1.
+// Each output adds the per-row partial sums of its taps: fewer rounding
+// steps in sequence than one long fma chain, which matters where a
 // projection amplifies u's error by up to beta/2 (twice on the morphology
 // path).
 template <int RP1, int NA, class Args>
@@ -330,17 +338,18 @@ __device__ __forceinline__ void strip_stencil(const float *__restrict__ src, int
   for (int k = 0; k < NA; ++k) out[k] = 0.f;
 #pragma unroll
   for (int rr = 0; rr < NA + 2 * R; ++rr) {
-    float v[BW];
+    float sp[R + 1];   // sp[0] = centre, sp[j] = src(+j) + src(-j)
+    sp[0] = src[rr * pitch + R];
 #pragma unroll
-    for (int q = 0; q < BW; ++q) v[q] = src[rr * pitch + q];
+    for (int j = 1; j <= R; ++j) sp[j] = src[rr * pitch + R + j] + src[rr * pitch + R - j];
 #pragma unroll
     for (int k = 0; k < NA; ++k) {
       const int p = rr - k - R;
       if (p >= -R && p <= R) {
         float part = 0.f;
 #pragma unroll
-        for (int q = -R; q <= R; ++q) {
-          if (p * p + q * q < RP1 * RP1) part = fmaf(a.w[(p + R) * BW + q + R], v[q + R], part);
+        for (int j = 0; j <= R; ++j) {
+          if (p * p + j * j < RP1 * RP1) part = fmaf(a.w[(p + R) * BW + j + R], sp[j], part);
         }
         out[k] += part;
       }

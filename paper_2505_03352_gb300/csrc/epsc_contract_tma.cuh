@@ -4,7 +4,10 @@
 // (component, Yee column, 2*nz floats).  One bulk tensor copy moves, for
 // all three components, the J-support window of BY consecutive columns --
 // the 32-byte sectors that hold planes k0 .. k0+nk -- into shared memory,
-// skipping the cladding planes between columns.  A block processes (chunk, wavelength)
+// skipping the cladding planes between columns.  A launch covers the columns
+// [col_lo, col_hi) (all of them, or one band of a pipelined call); a
+// chunk that runs past col_hi reads its last columns but writes no W for
+// them.  A block processes (chunk, wavelength)
 // items through an NSTAGE-deep ring: thread 0 keeps NSTAGE - 1 items in
 // flight (one mbarrier per stage, transaction-counted), all threads consume
 // from shared memory (eight lanes per column, 16 bytes each), and after the
@@ -37,6 +40,7 @@ struct __align__(128) ContractTmaArgsN {
   int nx, ny, k0, nk, nlambda;
   int x0;                                  // first float of the window in a column
   int bx;                                  // window width in floats (multiple of 8)
+  long col_lo, col_hi;                     // the launch's columns [col_lo, col_hi)
   float fs[EPS_MAX_LAMBDA][3];
   CUtensorMap maps[NMAPS];                 // [wavelength][field F/A]
 };
@@ -100,8 +104,9 @@ __global__ void __launch_bounds__(NTHREADS) contract_tma_kernel(const __grid_con
   float *smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
 
   const int tid = threadIdx.x;
-  const long ncol = (long)a.nx * a.ny;
-  const int nchunks = (int)((ncol + TMA_BY - 1) / TMA_BY);
+  const long ncol = (long)a.nx * a.ny;       // W plane stride
+  const long col_lo = a.col_lo;
+  const int nchunks = (int)((a.col_hi - col_lo + TMA_BY - 1) / TMA_BY);
   const int nl = a.nlambda;
   const int bx = a.bx;
   const int stage_floats = 6 * TMA_BY * bx;
@@ -126,8 +131,9 @@ __global__ void __launch_bounds__(NTHREADS) contract_tma_kernel(const __grid_con
     const int l = j % nl;
     float *dst = smem + (size_t)s * stage_floats;
     mbar_arrive_expect_tx(&full[s], stage_bytes);
-    tma_load_3d(dst, &a.maps[l * 2 + 0], a.x0, chunk * TMA_BY, 0, &full[s]);
-    tma_load_3d(dst + 3 * TMA_BY * bx, &a.maps[l * 2 + 1], a.x0, chunk * TMA_BY, 0, &full[s]);
+    const int c0 = (int)(col_lo + (long)chunk * TMA_BY);
+    tma_load_3d(dst, &a.maps[l * 2 + 0], a.x0, c0, 0, &full[s]);
+    tma_load_3d(dst + 3 * TMA_BY * bx, &a.maps[l * 2 + 1], a.x0, c0, 0, &full[s]);
   };
 
   if (tid == 0)
@@ -180,8 +186,8 @@ __global__ void __launch_bounds__(NTHREADS) contract_tma_kernel(const __grid_con
         acc2 += __shfl_xor_sync(0xffffffffu, acc2, off);
         acc3 += __shfl_xor_sync(0xffffffffu, acc3, off);
       }
-      const long col = (long)(blockIdx.x + (i / nl) * gridDim.x) * TMA_BY + row;
-      if (gl == 0 && col < ncol) {
+      const long col = col_lo + (long)(blockIdx.x + (i / nl) * gridDim.x) * TMA_BY + row;
+      if (gl == 0 && col < a.col_hi) {
         a.W[0 * ncol + col] = acc0;
         a.W[1 * ncol + col] = acc1;
         a.W[2 * ncol + col] = acc2;

@@ -40,6 +40,7 @@ struct ContractPackedArgs {
   float *W;                      // [4][nx][ny]
   int *err;                      // error flag (debug bounds checks)
   int nstage;                    // bulk-copy ring depth (contract_packed_bulk_kernel)
+  long col_lo, col_hi;           // contract_packed_bulk_kernel: the launch's columns
 };
 
 // Bulk-copy form of the packed contraction: PK_BY columns per chunk, one
@@ -216,8 +217,9 @@ __global__ void __launch_bounds__(PK_THREADS) contract_packed_bulk_kernel(
   unsigned char *ring =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(pk_raw) + 127) & ~uintptr_t(127));
   const int tid = threadIdx.x;
-  const long ncol = (long)a.nx * a.ny;
-  const long nchunks = (ncol + PK_BY - 1) / PK_BY;
+  const long ncol = (long)a.nx * a.ny;       // component and W plane stride
+  const long col_lo = a.col_lo, col_hi = a.col_hi;
+  const long nchunks = (col_hi - col_lo + PK_BY - 1) / PK_BY;
   const int nl = a.nlambda, ns = a.nstage;
   const unsigned colb = (unsigned)a.np * 4u;                 // bytes per column and component
   const unsigned stage_bytes = 6u * PK_BY * colb;
@@ -236,8 +238,8 @@ __global__ void __launch_bounds__(PK_THREADS) contract_packed_bulk_kernel(
     const int s = (int)(j % ns);
     const long chunk = blockIdx.x + (j / nl) * gridDim.x;
     const int l = (int)(j % nl);
-    const long col0 = chunk * PK_BY;
-    const unsigned n = (unsigned)min((long)PK_BY, ncol - col0);
+    const long col0 = col_lo + chunk * PK_BY;
+    const unsigned n = (unsigned)min((long)PK_BY, col_hi - col0);
     unsigned char *dst = ring + (size_t)s * stage_bytes;
     mbar_arrive_expect_tx(&full[s], 6u * n * colb);
 #pragma unroll
@@ -290,8 +292,8 @@ __global__ void __launch_bounds__(PK_THREADS) contract_packed_bulk_kernel(
       acc_in = __fadd_rn(acc_in, __fmul_rn(s_in, sc));
       if (c == 2) acc_face = __fadd_rn(acc_face, __fmul_rn(s_face, sc));
       if (l == nl - 1) {
-        const long gcol = (blockIdx.x + (i / nl) * gridDim.x) * PK_BY + col;
-        if (gcol < ncol) {
+        const long gcol = col_lo + (blockIdx.x + (i / nl) * gridDim.x) * PK_BY + col;
+        if (gcol < col_hi) {
           a.W[(size_t)c * ncol + gcol] = acc_in;
           if (c == 2) a.W[3 * (size_t)ncol + gcol] = acc_face;
         }

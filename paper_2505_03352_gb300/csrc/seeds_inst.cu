@@ -5,7 +5,9 @@
 // W_x; the same per W_y; dJ/dH_z per W_zf); dJ/dA_z is W_zi itself.  This
 // kernel runs once both the contraction and the stencil have completed
 // (ordinary stream order) and turns the factors into seeds in place, over
-// all regions of a call (one region for the single-region calls).  When the
+// all regions of a call (one region for the single-region calls), or over
+// one band of columns of a single region (pipelined calls: it then waits
+// only for that band's contraction).  When the
 // Eq. 1 surrogate is requested (single-region calls) it also adds
 // sum over columns of eps_col . W to *S, from the per-column eps values the
 // stencil left in epsc.
@@ -27,17 +29,19 @@ __global__ void __launch_bounds__(NTHREADS) seeds_kernel(const __grid_constant__
   // the scatter kernel queued behind may begin launching; it waits for this
   // grid before it reads the seeds
   griddep_launch_dependents();
-  if (a.n == 1 && (a.r[0].ncol & 3) == 0) {
+  const bool band = a.band_hi > 0;
+  if (a.n == 1 && (a.r[0].ncol & 3) == 0 && (a.band_lo & 3) == 0 && (a.band_hi & 3) == 0) {
     // one region whose maps are whole float4 rows (the workspace sections are
     // 256-byte aligned): four columns per thread, 16-byte accesses, the same
     // products element by element
     const SeedsRegion &rg = a.r[0];
     const long p4 = rg.ncol >> 2;
+    const long q0 = band ? a.band_lo >> 2 : 0, q1 = band ? a.band_hi >> 2 : p4;
     const float4 *W = reinterpret_cast<const float4 *>(rg.W);
     const float4 *E = reinterpret_cast<const float4 *>(a.epsc);
     float4 *s = reinterpret_cast<float4 *>(rg.seeds);
     double sum = 0.0;
-    for (long q = (long)blockIdx.x * NTHREADS + threadIdx.x; q < p4; q += (long)gridDim.x * NTHREADS) {
+    for (long q = q0 + (long)blockIdx.x * NTHREADS + threadIdx.x; q < q1; q += (long)gridDim.x * NTHREADS) {
       const float4 Wx = __ldg(W + q), Wy = __ldg(W + p4 + q);
       const float4 Wzi = __ldg(W + 2 * p4 + q), Wzf = __ldg(W + 3 * p4 + q);
       if (a.S) sum += dot4(__ldg(E + q), Wx) + dot4(__ldg(E + p4 + q), Wy) +
@@ -57,7 +61,8 @@ __global__ void __launch_bounds__(NTHREADS) seeds_kernel(const __grid_constant__
     return;
   }
   double sum = 0.0;
-  for (long c = (long)blockIdx.x * NTHREADS + threadIdx.x; c < a.ncol; c += (long)gridDim.x * NTHREADS) {
+  const long c0 = band ? a.band_lo : 0, c1 = band ? a.band_hi : a.ncol;
+  for (long c = c0 + (long)blockIdx.x * NTHREADS + threadIdx.x; c < c1; c += (long)gridDim.x * NTHREADS) {
     int k = 0;
     while (k + 1 < a.n && c >= a.r[k + 1].col_start) ++k;
     const SeedsRegion &rg = a.r[k];
