@@ -947,9 +947,11 @@ namespace {
 // kept: the contraction bands on a stream of the highest priority (2494 us
 // at 4 bands), the stencil as a persistent grid of two blocks per SM
 // (2377 / 508 us at 4 bands).
+// Packed (BF16 / FP16) fields keep the single-stream order: banding their
+// contraction (chunks of 128 columns) measured 1.171 -> 1.257 ms at the
+// 3000 x 3000, eight-wavelength call, whose shorter field stream leaves less
+// to hide and more to lose at each boundary.
 constexpr int PIPE_BANDS = 3;
-// (packed fields take the pipeline too once measured; off until then)
-constexpr bool PIPE_PACKED = false;
 static_assert(PIPE_BANDS <= MAX_PIPE_BANDS, "band events");
 
 // Highest Yee row of the seed maps that scatter tile row t reads, its
@@ -964,8 +966,7 @@ int scatter_seed_row_hi(const Resolved &r, int t) {
 
 struct PipeCall {
   const Resolved *r;
-  ContractTmaArgs *ta;          // prepared contraction (every column): complex64 fields,
-  ContractPackedArgs *pa;       // or packed fields (bulk-copy kernel); one is null
+  ContractTmaArgs *ta;          // prepared contraction (every column)
   FwdArgs *fa;                  // stencil arguments (seed factors: defer form)
   KernelEntry kf;
   size_t fsmem;
@@ -988,9 +989,9 @@ eps_status_t vjp_pipelined(const PipeCall &c, cudaStream_t s) {
   // Bands of whole rounds of the contraction grid (one chunk per block and
   // round), so every block of a band has the same number of chunks.
   const long ncol = (long)g.nx * g.ny;
-  const long chunk_cols = c.ta ? TMA_BY : PK_BY;
+  const long chunk_cols = TMA_BY;
   const long nchunks = (ncol + chunk_cols - 1) / chunk_cols;
-  const long per_round = (long)nsm * (c.ta ? CONTRACT_BLOCKS_PER_SM : PACKED_BLOCKS_PER_SM);
+  const long per_round = (long)nsm * CONTRACT_BLOCKS_PER_SM;
   const long rounds = (nchunks + per_round - 1) / per_round;
   const int nb = (int)std::max<long>(1, std::min<long>(PIPE_BANDS, rounds));
   const int T = (int)bwd_grid(g).y;
@@ -1003,8 +1004,7 @@ eps_status_t vjp_pipelined(const PipeCall &c, cudaStream_t s) {
     const long lo = std::min(ncol, rounds * b / nb * per_round * chunk_cols);
     const long hi =
         b == nb - 1 ? ncol : std::min(ncol, rounds * (b + 1) / nb * per_round * chunk_cols);
-    st = c.ta ? launch_contract_tma(c.ta, lo, hi, s) : launch_contract_packed(c.pa, lo, hi, s);
-    if (st != EPS_OK) return st;
+    if ((st = launch_contract_tma(c.ta, lo, hi, s)) != EPS_OK) return st;
     if (cudaEventRecord(aux->band[b], s) != cudaSuccess) return EPS_ERR_CUDA;
     if (b == 0 && (st = launch(c.fname, c.kf.fn, dim3((unsigned)c.fblocks), c.fsmem, c.fa,
                                aux->pipe, false)) != EPS_OK)
@@ -1119,21 +1119,11 @@ eps_status_t vjp_fused(const eps_problem_t *prob, const float *C, int32_t n_lamb
       std::unique_ptr<ContractTmaArgs> ta(new ContractTmaArgs);
       st = prepare_contract_tma(r.g, n_lambda, EF, EA, ca.fs, Wm, err, ta.get());
       if (st == EPS_OK) {
-        PipeCall pc{&r, ta.get(), nullptr, &fa, kf, smem, blocks, fname, Wm, seeds, pd4, ie2,
-                    dJdC, epsc, S, err};
+        PipeCall pc{&r, ta.get(), &fa, kf, smem, blocks, fname, Wm, seeds, pd4, ie2, dJdC, epsc,
+                    S, err};
         return vjp_pipelined(pc, s);
       }
       if (st != EPS_ERR_UNSUPPORTED) return st;
-    } else if (PIPE_PACKED) {
-      ContractPackedArgs pa;
-      bool bulk = false;
-      st = prepare_contract_packed(r.g, n_lambda, field_type, EF, EA, ca.fs, Wm, err, &pa, &bulk);
-      if (st != EPS_OK) return st;
-      if (bulk) {
-        PipeCall pc{&r, nullptr, &pa, &fa, kf, smem, blocks, fname, Wm, seeds, pd4, ie2, dJdC,
-                    epsc, S, err};
-        return vjp_pipelined(pc, s);
-      }
     }
   }
 
