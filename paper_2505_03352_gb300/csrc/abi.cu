@@ -951,8 +951,13 @@ namespace {
 // contraction (chunks of 128 columns) measured 1.171 -> 1.257 ms at the
 // 3000 x 3000, eight-wavelength call, whose shorter field stream leaves less
 // to hide and more to lose at each boundary.
-constexpr int PIPE_BANDS = 3;
-static_assert(PIPE_BANDS <= MAX_PIPE_BANDS, "band events");
+// cumulative share of the contraction's rounds at each band's end
+#ifndef EPSC_PIPE_SPLIT
+#define EPSC_PIPE_SPLIT 1.0 / 3, 2.0 / 3, 1.0
+#endif
+constexpr double PIPE_SPLIT[] = {EPSC_PIPE_SPLIT};
+constexpr int PIPE_NSPLIT = (int)(sizeof(PIPE_SPLIT) / sizeof(double));
+static_assert(PIPE_NSPLIT <= MAX_PIPE_BANDS, "band events");
 
 // Highest Yee row of the seed maps that scatter tile row t reads, its
 // bulk-copy boxes included (edge-replicate rule: no wrap).
@@ -993,44 +998,54 @@ eps_status_t vjp_pipelined(const PipeCall &c, cudaStream_t s) {
   const long nchunks = (ncol + chunk_cols - 1) / chunk_cols;
   const long per_round = (long)nsm * CONTRACT_BLOCKS_PER_SM;
   const long rounds = (nchunks + per_round - 1) / per_round;
-  const int nb = (int)std::max<long>(1, std::min<long>(PIPE_BANDS, rounds));
+  const int nb = (int)std::max<long>(1, std::min<long>(PIPE_NSPLIT, rounds));
+  auto band_end = [&](int b) {   // first round after band b
+    if (b >= nb - 1) return rounds;
+    if (nb < PIPE_NSPLIT) return rounds * (b + 1) / nb;
+    return std::min(rounds, std::max<long>(b + 1, (long)(rounds * PIPE_SPLIT[b] + 0.5)));
+  };
   const int T = (int)bwd_grid(g).y;
 
   if (cudaEventRecord(aux->pipe_fork, s) != cudaSuccess ||
       cudaStreamWaitEvent(aux->pipe, aux->pipe_fork, 0) != cudaSuccess)
     return EPS_ERR_CUDA;
-  int t_done = 0;
-  for (int b = 0; b < nb; ++b) {
-    const long lo = std::min(ncol, rounds * b / nb * per_round * chunk_cols);
-    const long hi =
-        b == nb - 1 ? ncol : std::min(ncol, rounds * (b + 1) / nb * per_round * chunk_cols);
-    if ((st = launch_contract_tma(c.ta, lo, hi, s)) != EPS_OK) return st;
-    if (cudaEventRecord(aux->band[b], s) != cudaSuccess) return EPS_ERR_CUDA;
-    if (b == 0 && (st = launch(c.fname, c.kf.fn, dim3((unsigned)c.fblocks), c.fsmem, c.fa,
-                               aux->pipe, false)) != EPS_OK)
-      return st;
-    if (cudaStreamWaitEvent(aux->pipe, aux->band[b], 0) != cudaSuccess) return EPS_ERR_CUDA;
-    if ((st = run_seeds_one(g, c.W, c.seeds, c.err, aux->pipe, c.S ? c.epsc : nullptr, c.S, lo,
-                            hi)) != EPS_OK)
-      return st;
-    // tile rows whose seed rows (all below the first incomplete Yee row) are done
-    int t_ready = T;
-    if (b < nb - 1) {
-      const long rows_done = hi / g.ny;
-      t_ready = t_done;
-      while (t_ready < T && scatter_seed_row_hi(r, t_ready) < rows_done) ++t_ready;
-    }
-    if (t_ready > t_done) {
-      if ((st = run_scatter(r, c.seeds, c.pd4, c.ie2, c.dJdC, c.err, aux->pipe, t_done, t_ready,
-                            false)) != EPS_OK)
+  auto bands = [&]() -> eps_status_t {
+    int t_done = 0;
+    for (int b = 0; b < nb; ++b) {
+      const long lo = b == 0 ? 0 : std::min(ncol, band_end(b - 1) * per_round * chunk_cols);
+      const long hi = b == nb - 1 ? ncol : std::min(ncol, band_end(b) * per_round * chunk_cols);
+      if ((st = launch_contract_tma(c.ta, lo, hi, s)) != EPS_OK) return st;
+      if (cudaEventRecord(aux->band[b], s) != cudaSuccess) return EPS_ERR_CUDA;
+      if (b == 0 && (st = launch(c.fname, c.kf.fn, dim3((unsigned)c.fblocks), c.fsmem, c.fa,
+                                 aux->pipe, false)) != EPS_OK)
         return st;
-      t_done = t_ready;
+      if (cudaStreamWaitEvent(aux->pipe, aux->band[b], 0) != cudaSuccess) return EPS_ERR_CUDA;
+      if ((st = run_seeds_one(g, c.W, c.seeds, c.err, aux->pipe, c.S ? c.epsc : nullptr, c.S, lo,
+                              hi)) != EPS_OK)
+        return st;
+      // tile rows whose seed rows (all below the first incomplete Yee row) are done
+      int t_ready = T;
+      if (b < nb - 1) {
+        const long rows_done = hi / g.ny;
+        t_ready = t_done;
+        while (t_ready < T && scatter_seed_row_hi(r, t_ready) < rows_done) ++t_ready;
+      }
+      if (t_ready > t_done) {
+        if ((st = run_scatter(r, c.seeds, c.pd4, c.ie2, c.dJdC, c.err, aux->pipe, t_done, t_ready,
+                              false)) != EPS_OK)
+          return st;
+        t_done = t_ready;
+      }
     }
-  }
-  if (cudaEventRecord(aux->pipe_join, aux->pipe) != cudaSuccess ||
-      cudaStreamWaitEvent(s, aux->pipe_join, 0) != cudaSuccess)
-    return EPS_ERR_CUDA;
-  return EPS_OK;
+    return EPS_OK;
+  };
+  st = bands();
+  // joined back even after a failed enqueue, so that work queued on `s`
+  // later never runs ahead of pipeline work already queued
+  const bool joined = cudaEventRecord(aux->pipe_join, aux->pipe) == cudaSuccess &&
+                      cudaStreamWaitEvent(s, aux->pipe_join, 0) == cudaSuccess;
+  if (st != EPS_OK) return st;
+  return joined ? EPS_OK : EPS_ERR_CUDA;
 }
 
 // The fused forward + Eq. 1 VJP of eps_vjp; with S non-null also the
@@ -1114,7 +1129,7 @@ eps_status_t vjp_fused(const eps_problem_t *prob, const float *C, int32_t n_lamb
     std::lock_guard<std::mutex> lk(g_prof_mu);
     prof = g_prof_on;
   }
-  if (PIPE_BANDS > 1 && !prof && n_lambda > 0 && form.defer == 1 && r.g.bc == EPS_BC_CLAMP) {
+  if (PIPE_NSPLIT > 1 && !prof && n_lambda > 0 && form.defer == 1 && r.g.bc == EPS_BC_CLAMP) {
     if (field_type == EPS_FIELD_C64) {
       std::unique_ptr<ContractTmaArgs> ta(new ContractTmaArgs);
       st = prepare_contract_tma(r.g, n_lambda, EF, EA, ca.fs, Wm, err, ta.get());
