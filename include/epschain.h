@@ -553,6 +553,17 @@ eps_status_t eps_profile_start(void);
 eps_status_t eps_profile_stop(eps_profile_entry_t *entries, int32_t max_entries,
                               int32_t *n_entries);
 
+/*
+ * Number of kernel launches this library has made in the process, on every
+ * device and stream (a host-side counter, incremented when a launch is
+ * accepted; no synchronisation).  The difference of two readings counts the
+ * launches of the calls made in between, whatever form they took (a band
+ * pipeline launches more kernels than the single-stream order).
+ * EPS_ERR_INVALID_ARG for a null pointer.  Instrumentation; the paper has no
+ * counterpart.
+ */
+eps_status_t eps_launch_count(uint64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,7 +10,8 @@ from .epschain import (BatchedVjp, eps_batched_workspace_size, eps_forward_batch
                        EPS_BC_CLAMP, EPS_BC_PERIODIC, EPS_FIELD_C64, EPS_FIELD_BF16X2_SCALED,
                        EPS_FIELD_F16X2_SCALED, EPS_FLAG_OFFDIAG, EPS_FLAG_NORMALS_3D, EpsError, PreparedVjp, Problem,
                        eps_field_pack, eps_forward, eps_packed_field_bytes,
-                       eps_profile_start, eps_profile_stop, eps_set_l2_fetch_granularity,
+                       eps_profile_start, eps_profile_stop, eps_launch_count,
+                       eps_set_l2_fetch_granularity,
                        eps_selftest_timeout, eps_selftest_bounds,
                        eps_status_string, eps_sync_status,
                        eps_vjp, eps_vjp_real, eps_vjp_surrogate, eps_workspace_size, lib,
@@ -26,7 +27,8 @@ __all__ = [
     "EPS_BC_CLAMP", "EPS_BC_PERIODIC", "EPS_FIELD_C64", "EPS_FIELD_BF16X2_SCALED",
     "EPS_FIELD_F16X2_SCALED", "EPS_FLAG_OFFDIAG", "EPS_FLAG_NORMALS_3D", "EpsError", "PreparedVjp", "Problem", "eps_forward",
     "eps_field_pack", "eps_packed_field_bytes",
-    "eps_profile_start", "eps_profile_stop", "eps_set_l2_fetch_granularity",
+    "eps_profile_start", "eps_profile_stop", "eps_launch_count",
+    "eps_set_l2_fetch_granularity",
     "eps_selftest_timeout", "eps_selftest_bounds", "eps_status_string",
     "eps_sync_status", "eps_vjp",
     "eps_vjp_real", "eps_vjp_surrogate", "eps_workspace_size", "lib",

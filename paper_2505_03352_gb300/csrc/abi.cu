@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <memory>
 #include <mutex>
 #include <set>
@@ -178,6 +179,9 @@ eps_status_t sm_count(int *n) {
 // (programmatic dependent launch); it must then wait on that grid
 // (griddepcontrol.wait) before reading its results.  While profiling, each
 // launch is bracketed by events and launched without overlap.
+// Kernel launches made by the library in this process (eps_launch_count).
+std::atomic<unsigned long long> g_launch_count{0};
+
 eps_status_t launch(const char *name, const void *fn, dim3 grid, size_t smem, void *args,
                     cudaStream_t s, bool pdl = false, unsigned block = NTHREADS) {
   eps_status_t st = prepare(fn, smem);
@@ -207,6 +211,7 @@ eps_status_t launch(const char *name, const void *fn, dim3 grid, size_t smem, vo
   }
   void *params[] = {args};
   if (cudaLaunchKernelExC(&cfg, fn, params) != cudaSuccess) return EPS_ERR_CUDA;
+  g_launch_count.fetch_add(1, std::memory_order_relaxed);
   if (prof) {
     if (cudaEventRecord(rec.e1, s) != cudaSuccess) return EPS_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -506,10 +511,12 @@ eps_status_t run_contract_tma_real(const Geometry &g, const float *G, float *Wm,
 }
 
 // Launch shape of the bulk-copy packed contraction (swept at the 3000 x
-// 3000, eight-wavelength BF16 call: 2 x 2 stages of 128 columns, with the
-// stencil beside it, 1.23 ms; 2 x 3 stages 1.35 ms; the register-load
-// kernel, which fills every SM slot, 1.41 ms).
-constexpr int PACKED_BLOCKS_PER_SM = 2;
+// 3000, eight-wavelength BF16 call: three blocks per SM of two stages of 96
+// columns, 55 KB each, with the stencil beside them, 1.140 ms; two of 128
+// columns 1.165-1.171 ms; 2 x 3 stages of 128 columns 1.35 ms; the
+// register-load kernel, which fills every SM slot, 1.41 ms; more shapes at
+// PK_BY).
+constexpr int PACKED_BLOCKS_PER_SM = 3;
 constexpr int PACKED_NSTAGE = 2;
 
 // Packed planes per column (multiple of 4) and bytes of one packed field.
@@ -548,10 +555,10 @@ eps_status_t prepare_contract_packed(const Geometry &g, int n_lambda, int type,
 }
 
 // The bulk-copy packed contraction over the columns [col_lo, col_hi): a ring
-// of PACKED_NSTAGE stages of 6 x PK_BY x 4 np bytes (37 KB at nk = 11) in
-// PACKED_BLOCKS_PER_SM blocks per SM, about 74 KB per block, so stencil
-// blocks (32 KB with one eps_hat component staged per round) still fit
-// beside the two.
+// of PACKED_NSTAGE stages of 6 x PK_BY x 4 np bytes (27.6 KB at nk = 11) in
+// PACKED_BLOCKS_PER_SM blocks per SM, about 55 KB per block, so a stencil
+// block (34 KB with one eps_hat component staged per round) still fits
+// beside the three.
 eps_status_t launch_contract_packed(ContractPackedArgs *pa, long col_lo, long col_hi,
                                     cudaStream_t s) {
   int nsm = 0;
@@ -951,11 +958,12 @@ namespace {
 // contraction (chunks of 128 columns) measured 1.171 -> 1.257 ms at the
 // 3000 x 3000, eight-wavelength call, whose shorter field stream leaves less
 // to hide and more to lose at each boundary.
-// cumulative share of the contraction's rounds at each band's end
-#ifndef EPSC_PIPE_SPLIT
-#define EPSC_PIPE_SPLIT 1.0 / 3, 2.0 / 3, 1.0
-#endif
-constexpr double PIPE_SPLIT[] = {EPSC_PIPE_SPLIT};
+// Cumulative share of the contraction's rounds at each band's end.  Uneven
+// splits moved the two workloads apart by about 1 % either way (one box:
+// 0.5 / 0.85 / 1: 3000 x 3000 2372 us, 2000 x 2000 514 us; 0.6 / 1: 2393 /
+// 501 us; 0.35 / 0.65 / 0.87 / 1: 2379 / 512 us; equal thirds 2394 / 505
+// us), so the bands stay equal.
+constexpr double PIPE_SPLIT[] = {1.0 / 3, 2.0 / 3, 1.0};
 constexpr int PIPE_NSPLIT = (int)(sizeof(PIPE_SPLIT) / sizeof(double));
 static_assert(PIPE_NSPLIT <= MAX_PIPE_BANDS, "band events");
 
@@ -1283,6 +1291,7 @@ eps_status_t eps_field_pack(const eps_problem_t *prob, int32_t field_type, const
   void *args[] = {&d, &pa.type};
   if (cudaLaunchKernel(pack_finish_entry(), dim3(1), dim3(32), args, 0, s) != cudaSuccess)
     return EPS_ERR_CUDA;
+  g_launch_count.fetch_add(1, std::memory_order_relaxed);
   return EPS_OK;
 }
 
@@ -1328,6 +1337,12 @@ eps_status_t eps_set_l2_fetch_granularity(int32_t bytes, int32_t *previous) {
   if (previous) *previous = (int32_t)old;
   if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes) != cudaSuccess)
     return EPS_ERR_CUDA;
+  return EPS_OK;
+}
+
+eps_status_t eps_launch_count(uint64_t *count) {
+  if (!count) return EPS_ERR_INVALID_ARG;
+  *count = g_launch_count.load(std::memory_order_relaxed);
   return EPS_OK;
 }
 
@@ -2074,6 +2089,8 @@ eps_status_t launch_kernel(const char *name, const void *fn, dim3 grid, size_t s
                            cudaStream_t s, bool pdl) {
   return launch(name, fn, grid, smem, args, s, pdl);
 }
+
+void note_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
 
 eps_status_t subpixel_factor_offset(const eps_problem_t *prob, size_t *offset, size_t *ws_needed) {
   Resolved r;

@@ -45,7 +45,9 @@ eps_status_t eps_opt_init(const eps_opt_t *opt, eps_opt_state_t *state, eps_stre
   if (!state || !aligned(state, 4)) return EPS_ERR_INVALID_ARG;
   const float beta1 = (float)schedule(1, opt, opt->beta_max0);
   opt_init_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(state, beta1, opt->beta_max0);
-  return cudaGetLastError() == cudaSuccess ? EPS_OK : EPS_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return EPS_ERR_CUDA;
+  epsc_host::note_launch();
+  return EPS_OK;
 }
 
 eps_status_t eps_opt_step(const eps_problem_t *prob, const eps_morph_t *morph, const eps_opt_t *opt,

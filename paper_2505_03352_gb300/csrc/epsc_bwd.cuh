@@ -84,12 +84,6 @@ __device__ __forceinline__ void sobel_t_weights(int t, int n, int bc, float (&wd
   }
 }
 
-// 16-byte asynchronous copy; both addresses 16-byte aligned.
-__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-
 // One tile (subpixel rows a0 .., columns b0 ..) of one region `rg`.  With
 // TMA, `maps` points at the region's four tensor maps of the staged inputs
 // in the kernel parameters (bwd_tma_kernel: single region; the batched

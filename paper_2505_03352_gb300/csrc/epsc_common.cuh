@@ -264,6 +264,12 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool val
                : "memory");
 }
 
+// 16-byte asynchronous copy; both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }

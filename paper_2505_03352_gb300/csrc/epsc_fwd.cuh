@@ -26,10 +26,13 @@ struct FwdSmem {
   static constexpr int R = RP1 - 1;
   static constexpr int CA = UA + 2 * R;
   static constexpr int CB = UB + 2 * R;
+  // row pitch of the staged C tile: whole 16-byte runs with room for a row
+  // that starts up to 3 floats after a 16-byte boundary
+  static constexpr int CBP = (CB + 3 + 3) & ~3;
   static constexpr int HP = TJ + 2;              // pitch of the halo cell maps
   static constexpr int HN = (TI + 2) * HP;
   static constexpr int OFF_C = 0;
-  static constexpr int OFF_U = OFF_C + CA * CB;
+  static constexpr int OFF_U = OFF_C + CA * CBP;
   static constexpr int OFF_E = OFF_U + UA * UB;
   static constexpr int OFF_IE = OFF_E + UA * UB;
   static constexpr int OFF_UX = OFF_IE + UA * UB;
@@ -115,14 +118,34 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
   griddep_launch_dependents();
 
   // ---- 1. control tile with halo (asynchronous copies) ----------------
-  for (int idx = tid; idx < S::CA * CB; idx += NTHREADS) {
-    const int r = idx / CB;
-    const int c = idx - r * CB;
-    const int ga = bc_map_t<BC>(ca0 + r, g.mx);
-    const int gb = bc_map_t<BC>(cb0 + c, g.my);
-    const size_t o = (size_t)ga * g.my + gb;
-    const bool ok = EPSC_IN_BOUNDS(o, 1, (size_t)g.mx * g.my, a.err);
-    cp_async4(sC + idx, rg.C + (ok ? o : 0), ok);
+  // A tile whose halo lies inside the region, in a control map whose rows
+  // are whole 16-byte runs, copies 16 bytes at a time from the 16-byte
+  // boundary at or below its first column (the staged view is shifted by
+  // the remainder, csh); the others copy element by element with the
+  // boundary rule applied.  Every copy stays inside the map.
+  constexpr int CBP = S::CBP;
+  const int xa = cb0 & ~3;                       // (floor to a multiple of 4)
+  const int ncv = (cb0 + CB - xa + 3) >> 2;      // float4 per row
+  const bool cvec = (g.my & 3) == 0 && ((uintptr_t)rg.C & 15) == 0 && ca0 >= 0 &&
+                    ca0 + S::CA <= g.mx && xa >= 0 && xa + 4 * ncv <= g.my;
+  const int csh = cvec ? cb0 - xa : 0;
+  if (cvec) {
+    for (int idx = tid; idx < S::CA * ncv; idx += NTHREADS) {
+      const int r = idx / ncv, k = idx - r * ncv;
+      const size_t o = (size_t)(ca0 + r) * g.my + xa + 4 * k;
+      if (!EPSC_IN_BOUNDS(o, 4, (size_t)g.mx * g.my, a.err)) continue;
+      cp_async16(sC + r * CBP + 4 * k, rg.C + o);
+    }
+  } else {
+    for (int idx = tid; idx < S::CA * CB; idx += NTHREADS) {
+      const int r = idx / CB;
+      const int c = idx - r * CB;
+      const int ga = bc_map_t<BC>(ca0 + r, g.mx);
+      const int gb = bc_map_t<BC>(cb0 + c, g.my);
+      const size_t o = (size_t)ga * g.my + gb;
+      const bool ok = EPSC_IN_BOUNDS(o, 1, (size_t)g.mx * g.my, a.err);
+      cp_async4(sC + r * CBP + c, rg.C + (ok ? o : 0), ok);
+    }
   }
   cp_async_wait_all();
   __syncthreads();
@@ -140,7 +163,7 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
     const int col = item - s * UB;
     const int r0 = s * NA_F;
     float hi[NA_F];
-    strip_stencil<RP1, NA_F>(sC + r0 * CB + col, CB, a, hi);
+    strip_stencil<RP1, NA_F>(sC + csh + r0 * CBP + col, CBP, a, hi);
 #pragma unroll
     for (int k = 0; k < NA_F; ++k) {
       const int o = (r0 + k) * UB + col;

@@ -25,6 +25,9 @@ eps_status_t check_vjp_args(const eps_problem_t *prob, const float *C, int32_t n
 eps_status_t launch_kernel(const char *name, const void *fn, dim3 grid, size_t smem, void *args,
                            cudaStream_t s, bool pdl);
 
+// Count one kernel launch made outside launch_kernel (eps_launch_count).
+void note_launch();
+
 // Byte offset, inside an eps_vjp / eps_vjp_real workspace for `prob`, of
 // the per-subpixel factor (beta/2)(eps_core - eps_clad) rho (1 - rho)
 // [mx][my] that the stencil pass writes, and the workspace size.

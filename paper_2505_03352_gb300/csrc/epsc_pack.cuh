@@ -45,12 +45,15 @@ struct ContractPackedArgs {
 
 // Bulk-copy form of the packed contraction: PK_BY columns per chunk, one
 // thread per (column, component) of a chunk.  Wide chunks make each bulk
-// copy one long contiguous run (6 KB per component at nk = 11): measured at
-// the 3000 x 3000, eight-wavelength BF16 call, 128 columns stream the packed
-// planes in 0.90 ms where 64 or 32 take 1.28 or 2.26 ms (a fixed cost per
-// ring item, whatever the ring depth) and 256 columns at one block per SM
-// 1.26 ms.
-constexpr int PK_BY = 128;
+// copy one long contiguous run (4.5 KB per component at nk = 11).  Measured
+// at the 3000 x 3000, eight-wavelength BF16 call: with two blocks per SM,
+// 128 columns stream the packed planes in 0.90 ms where 64 or 32 take 1.28
+// or 2.26 ms (a fixed cost per ring item, whatever the ring depth), and 256
+// columns at one block per SM 1.26 ms; the whole call at 96 columns and
+// three blocks per SM 1.140 ms, against 1.165-1.171 ms at 128 and two (80
+// columns and three blocks 1.204, 64 and four 1.176, 64 and five 1.245,
+// 96 with three stages and two blocks 1.382).
+constexpr int PK_BY = 96;
 constexpr int PK_THREADS = 3 * PK_BY;
 constexpr int PK_MAX_STAGE = 8;
 

@@ -114,6 +114,7 @@ _PROTOS = {
     "eps_field_pack": (ctypes.c_int, [ctypes.POINTER(eps_problem_t), ctypes.c_int32, _VP, _VP,
                                       ctypes.c_size_t, _VP]),
     "eps_profile_start": (ctypes.c_int, []),
+    "eps_launch_count": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
     "eps_set_l2_fetch_granularity": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "eps_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
     "eps_selftest_bounds": (ctypes.c_int, [ctypes.c_void_p]),
@@ -578,6 +579,14 @@ def eps_set_l2_fetch_granularity(nbytes: int) -> int:
 
 def eps_profile_start():
     _check(lib().eps_profile_start(), "eps_profile_start")
+
+
+def eps_launch_count() -> int:
+    """Kernel launches the library has made in this process (host counter;
+    the difference of two readings counts the calls in between)."""
+    n = ctypes.c_uint64(0)
+    _check(lib().eps_launch_count(ctypes.byref(n)), "eps_launch_count")
+    return n.value
 
 
 def eps_profile_stop(max_entries: int = 32):

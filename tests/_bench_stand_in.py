@@ -23,7 +23,7 @@ from paper_2505_03352_gb300 import synth  # noqa: E402
 
 def main():
     CPU = torch.device("cpu")
-    launch_count = {"n": 0}
+    launch_count = {"n": 0, "total": 0}
 
 
     class FakeStream:
@@ -85,7 +85,8 @@ def main():
 
     class FakeLib:
         """Every entry returns EPS_OK; eps_profile_stop reports one contraction
-        launch per profiled step so the roofline arithmetic has numbers."""
+        launch per profiled step so the roofline arithmetic has numbers, and
+        eps_launch_count four launches per call."""
 
         def __getattr__(self, name):
             def entry(*args):
@@ -98,8 +99,11 @@ def main():
                     launch_count["n"] = 0
                 elif name == "eps_profile_start":
                     launch_count["n"] = 0
+                elif name == "eps_launch_count":
+                    args[0]._obj.value = launch_count["total"]
                 elif name.startswith("eps_vjp") or name.startswith("eps_forward"):
                     launch_count["n"] += 1
+                    launch_count["total"] += 4
                 return eb.EPS_OK
             return entry
 

@@ -293,3 +293,16 @@ def test_debug_bounds_entry_is_declared_and_exported(L):
     # a release build answers the bounds self-test with EPS_ERR_UNSUPPORTED
     # before any launch
     assert L.eps_selftest_bounds(None) == 4               # EPS_ERR_UNSUPPORTED
+
+
+def test_launch_counter_reads_without_a_launch(L):
+    # a host-side counter: readable with no GPU, unchanged by calls that
+    # return before any launch, and a null pointer is an argument error
+    import ctypes
+    a = ec.eps_launch_count()
+    assert a >= 0
+    assert L.eps_launch_count(None) == 1          # EPS_ERR_INVALID_ARG
+    p = ec.Problem(mx=64, my=48, nz=16, radius=3.0, beta=8.0).c_struct()
+    bad = ctypes.c_void_p(0)
+    L.eps_forward(ctypes.byref(p), bad, bad, bad, None)   # rejected on the host
+    assert ec.eps_launch_count() == a
