@@ -514,6 +514,10 @@ eps_status_t eps_selftest_bounds(eps_stream_t stream);
  *     the GPU (different streams, or host threads without ordering) race and
  *     must be serialised by the caller.  Nothing in the array needs to start
  *     at zero; it keeps whatever the last call left there.
+ *   - Streams as in eps_vjp: a problem of more than one wave of stencil
+ *     tiles runs as its band pipeline, whose first call on a device creates
+ *     the library's pipeline stream and events (no device memory); make
+ *     such a call once before any stream capture as well.
  */
 #define EPS_STATIC_WS_BYTES (16 * 1024 * 1024)
 eps_status_t eps_vjp_static(const eps_problem_t *prob, const float *C, int32_t n_lambda,
