@@ -342,17 +342,56 @@ __device__ __forceinline__ void fwd_tile(const Args &a, const FwdRegion &rg, con
                               (comp < 3 ? 3 : (rg.normals3d ? 4 : 2)) * cplane, a.err))
             continue;
           float4 *dst = reinterpret_cast<float4 *>(base + roff);
-          for (int f0 = 0; f0 < nf4; f0 += 32) {
-            const int f = f0 + cc;
-            const int jj = min(f / nz4, 31);
-            const float v = __shfl_sync(0xffffffffu, vm, jj);
-            const float vf = __shfl_sync(0xffffffffu, ezf3, jj);
-            if (f < nf4) {
-              const int k = 4 * (f - (f / nz4) * nz4);
+          if ((32 % nz4) == 0) {
+            // nz4 divides 32, so a lane keeps the same four planes k .. k+3
+            // at every step: classify them once per component (the owning
+            // column's value, its negation, the face value, or a constant)
+            const int k = 4 * (cc % nz4);
+            int kind[4];
+            float cst[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int kk = k + q;
+              const bool slab = kk >= g.k0 + 1 && kk <= g.k0 + g.nk;
+              cst[q] = 0.f;
+              if (comp < 2) {
+                kind[q] = slab ? 0 : 3;
+                cst[q] = outv;
+              } else if (comp == 2) {
+                const bool inside = kk >= g.k0 + 1 && kk <= g.k0 + g.nk - 1;
+                const bool face = kk == g.k0 || kk == g.k0 + g.nk;
+                kind[q] = inside ? 0 : (face ? 2 : 3);
+                cst[q] = outv;
+              } else if (comp <= 4) {
+                kind[q] = slab ? 0 : 3;
+              } else {
+                kind[q] = kk == g.k0 ? 0 : (kk == g.k0 + g.nk ? 1 : 3);
+              }
+            }
+            const int jbase = cc / nz4;
+            for (int f0 = 0; f0 < nf4; f0 += 32) {
+              const int jj = min(f0 / nz4 + jbase, 31);
+              const float v = __shfl_sync(0xffffffffu, vm, jj);
+              const float vf = comp == 2 ? __shfl_sync(0xffffffffu, ezf3, jj) : 0.f;
               float t[4];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) t[q] = plane_value(comp, k + q, g.k0, g.nk, v, v, vf, outv);
-              __stcs(dst + f, make_float4(t[0], t[1], t[2], t[3]));
+              for (int q = 0; q < 4; ++q)
+                t[q] = kind[q] == 0 ? v : (kind[q] == 1 ? -v : (kind[q] == 2 ? vf : cst[q]));
+              if (f0 + cc < nf4) __stcs(dst + f0 + cc, make_float4(t[0], t[1], t[2], t[3]));
+            }
+          } else {
+            for (int f0 = 0; f0 < nf4; f0 += 32) {
+              const int f = f0 + cc;
+              const int jj = min(f / nz4, 31);
+              const float v = __shfl_sync(0xffffffffu, vm, jj);
+              const float vf = __shfl_sync(0xffffffffu, ezf3, jj);
+              if (f < nf4) {
+                const int k = 4 * (f - (f / nz4) * nz4);
+                float t[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) t[q] = plane_value(comp, k + q, g.k0, g.nk, v, v, vf, outv);
+                __stcs(dst + f, make_float4(t[0], t[1], t[2], t[3]));
+              }
             }
           }
         }
