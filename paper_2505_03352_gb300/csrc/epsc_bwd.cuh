@@ -329,7 +329,31 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
 
   // ---- du on the du region (in place over P' deps / 4) -----------------------
   const float q4 = 0.25f;
-  {
+  // A du region clear of the edge-replicate fold (every subpixel inside the
+  // region, none on row or column 0 or the last shifted cell; always under
+  // the wrap rule) has unit multiplicities: the same values without the
+  // edge logic.
+  const bool du_plain = !clamp || (da_lo >= 1 && da_lo + DA <= g.mx - 1 && db_lo >= 1 &&
+                                   db_lo + DB <= g.my - 1);
+  if (du_plain) {
+    const FastDiv ddb((unsigned)DB);
+    for (int idx = tid; idx < DA * DB; idx += NTHREADS) {
+      const int r = (int)ddb.div((unsigned)idx), c = idx - r * DB;
+      const int va = da_lo + r, vb = db_lo + c;
+      const float pd4 = sU[r * DBP + c];
+      const float ie2 = sIE2[r * DBP + c];
+      const int ic = (va >> 1) - ci_lo, is = ((va + 1) >> 1) - ci_lo;
+      const int jc = (vb >> 1) - cj_lo, js = ((vb + 1) >> 1) - cj_lo;
+      const int ox = ic * S::NCJ + js;
+      const int oy = is * S::NCJ + jc;
+      const int oz = is * S::NCJ + js;
+      const float de = (sSeed[0 * S::NC + ox] - sSeed[1 * S::NC + ox] * ie2) +
+                       (sSeed[2 * S::NC + oy] - sSeed[3 * S::NC + oy] * ie2) +
+                       (sSeed[4 * S::NC + oz] - sSeed[5 * S::NC + oz] * ie2);
+      const float dus = sdU[0 * S::NC + ox] + sdU[1 * S::NC + oy];
+      sU[r * DBP + c] = fmaf(pd4, de, q4 * dus);
+    }
+  } else {
     const FastDiv ddb((unsigned)DB);
     for (int idx = tid; idx < DA * DB; idx += NTHREADS) {
       const int r = (int)ddb.div((unsigned)idx), c = idx - r * DB;
@@ -375,6 +399,16 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
   __syncthreads();
 
   // ---- fold extended positions onto the edge and write ------------------
+  if (ga_lo == a0 && gb_lo == b0 && ga_hi == aend && gb_hi == bend) {
+    // no extended positions: each output is its own K^T result
+    for (int r = ty; r < aend - a0; r += 8) {
+      for (int c = tx; c < bend - b0; c += 32) {
+        const size_t go = (size_t)(a0 + r) * g.my + b0 + c;
+        if (EPSC_IN_BOUNDS(go, 1, (size_t)g.mx * g.my, a.err)) rg.dJdC[go] = sdc[r * S::GB_MAX + c];
+      }
+    }
+    return;
+  }
   for (int r = ty; r < aend - a0; r += 8) {
     const int ga = a0 + r;
     int ra0 = ga - ga_lo, ra1 = ra0;
