@@ -44,18 +44,25 @@ __global__ void __launch_bounds__(NTHREADS) seeds_kernel(const __grid_constant__
     for (long q = q0 + (long)blockIdx.x * NTHREADS + threadIdx.x; q < q1; q += (long)gridDim.x * NTHREADS) {
       const float4 Wx = __ldg(W + q), Wy = __ldg(W + p4 + q);
       const float4 Wzi = __ldg(W + 2 * p4 + q), Wzf = __ldg(W + 3 * p4 + q);
+      // every factor is loaded before the first store: the planes share one
+      // base pointer, so loads after a store would wait for it
+      const float4 fax = s[S_DAX * p4 + q], fhx = s[S_DHX * p4 + q];
+      const float4 gxx = s[S_GXX * p4 + q], gyx = s[S_GYX * p4 + q];
+      const float4 fay = s[S_DAY * p4 + q], fhy = s[S_DHY * p4 + q];
+      const float4 gxy = s[S_GXY * p4 + q], gyy = s[S_GYY * p4 + q];
+      const float4 fhz = s[S_DHZ * p4 + q];
       if (a.S) sum += dot4(__ldg(E + q), Wx) + dot4(__ldg(E + p4 + q), Wy) +
                       dot4(__ldg(E + 2 * p4 + q), Wzi) + dot4(__ldg(E + 3 * p4 + q), Wzf);
-      s[S_DAX * p4 + q] = mul4(s[S_DAX * p4 + q], Wx);
-      s[S_DHX * p4 + q] = mul4(s[S_DHX * p4 + q], Wx);
-      s[S_GXX * p4 + q] = mul4(s[S_GXX * p4 + q], Wx);
-      s[S_GYX * p4 + q] = mul4(s[S_GYX * p4 + q], Wx);
-      s[S_DAY * p4 + q] = mul4(s[S_DAY * p4 + q], Wy);
-      s[S_DHY * p4 + q] = mul4(s[S_DHY * p4 + q], Wy);
-      s[S_GXY * p4 + q] = mul4(s[S_GXY * p4 + q], Wy);
-      s[S_GYY * p4 + q] = mul4(s[S_GYY * p4 + q], Wy);
+      s[S_DAX * p4 + q] = mul4(fax, Wx);
+      s[S_DHX * p4 + q] = mul4(fhx, Wx);
+      s[S_GXX * p4 + q] = mul4(gxx, Wx);
+      s[S_GYX * p4 + q] = mul4(gyx, Wx);
+      s[S_DAY * p4 + q] = mul4(fay, Wy);
+      s[S_DHY * p4 + q] = mul4(fhy, Wy);
+      s[S_GXY * p4 + q] = mul4(gxy, Wy);
+      s[S_GYY * p4 + q] = mul4(gyy, Wy);
       s[S_DAZ * p4 + q] = Wzi;
-      s[S_DHZ * p4 + q] = mul4(s[S_DHZ * p4 + q], Wzf);
+      s[S_DHZ * p4 + q] = mul4(fhz, Wzf);
     }
     if (a.S) block_add_to(a.S, sum);   // uniform over the grid
     return;
@@ -71,16 +78,19 @@ __global__ void __launch_bounds__(NTHREADS) seeds_kernel(const __grid_constant__
     const float Wx = __ldg(rg.W + j), Wy = __ldg(rg.W + p + j);
     const float Wzi = __ldg(rg.W + 2 * p + j), Wzf = __ldg(rg.W + 3 * p + j);
     float *s = rg.seeds + j;
-    s[S_DAX * p] *= Wx;
-    s[S_DHX * p] *= Wx;
-    s[S_GXX * p] *= Wx;
-    s[S_GYX * p] *= Wx;
-    s[S_DAY * p] *= Wy;
-    s[S_DHY * p] *= Wy;
-    s[S_GXY * p] *= Wy;
-    s[S_GYY * p] *= Wy;
+    const float fax = s[S_DAX * p], fhx = s[S_DHX * p], gxx = s[S_GXX * p], gyx = s[S_GYX * p];
+    const float fay = s[S_DAY * p], fhy = s[S_DHY * p], gxy = s[S_GXY * p], gyy = s[S_GYY * p];
+    const float fhz = s[S_DHZ * p];
+    s[S_DAX * p] = fax * Wx;
+    s[S_DHX * p] = fhx * Wx;
+    s[S_GXX * p] = gxx * Wx;
+    s[S_GYX * p] = gyx * Wx;
+    s[S_DAY * p] = fay * Wy;
+    s[S_DHY * p] = fhy * Wy;
+    s[S_GXY * p] = gxy * Wy;
+    s[S_GYY * p] = gyy * Wy;
     s[S_DAZ * p] = Wzi;
-    s[S_DHZ * p] *= Wzf;
+    s[S_DHZ * p] = fhz * Wzf;
     if (a.S && a.n == 1) {
       const float *e = a.epsc + j;
       sum += fmaf(e[0], Wx, e[p] * Wy) + fmaf(e[2 * p], Wzi, e[3 * p] * Wzf);
