@@ -51,6 +51,7 @@ struct BwdSmem {
   static constexpr int DA_BOX = TA + 2 * R;
   // bytes the four bulk copies of such a tile deliver
   static constexpr unsigned TMA_BYTES = 4u * (2 * DBP * DA_BOX + 6 * NC + 4 * NG);
+  static constexpr unsigned TMA_BYTES_G = 4u * (4 * NG);   // the Sobel seeds' box alone
   static constexpr size_t BYTES = sizeof(float) * TOTAL;
 };
 
@@ -136,7 +137,10 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
   // shg).  The staged values are those of the element-wise gather below,
   // which every other tile (and the batched launches) takes.
   bool staged = false;
+  bool rest_pending = false;   // bulk copies of everything but the Sobel seeds in flight
   int sh = 0, shj = 0, shg = 0;
+  __shared__ uint64_t s_bar[2];
+  __shared__ int s_fail;
   if constexpr (TMA) {
     // (the sections sit on 128-byte boundaries of the dynamic shared memory,
     // declared 128-byte aligned; a base that were not falls back to the
@@ -144,31 +148,35 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
     if (maps && R >= 2 && (smem_addr(bwd_smem) & 127u) == 0u && da_lo >= 0 && da_lo + DA <= g.mx &&
         db_lo >= 0 && db_lo + DB <= g.my && ci_lo >= 1 && ci_lo + NCI + 1 <= g.nx && cj_lo >= 1 &&
         cj_lo + NCJ + 1 <= g.ny) {
-      __shared__ uint64_t bar;
-      __shared__ int s_fail;
       const int xa = db_lo & ~3, xs = cj_lo & ~3, xg = (cj_lo - 1) & ~3;
       sh = db_lo - xa;
       shj = cj_lo - xs;
       shg = cj_lo - 1 - xg;
+      // two barriers: the Sobel seeds' box (Sobel^T starts on it) and the
+      // other three (waited for after Sobel^T, below)
       if (tid == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        mbar_arrive_expect_tx(&bar, S::TMA_BYTES);
-        tma_load_3d(sU, &maps[0], xa, da_lo, 0, &bar);
-        tma_load_3d(sIE2, &maps[1], xa, da_lo, 0, &bar);
-        tma_load_3d(sSeed, &maps[2], xs, ci_lo, S_DAX, &bar);
-        tma_load_3d(sG, &maps[3], xg, ci_lo - 1, S_GXX, &bar);
+        mbar_arrive_expect_tx(&s_bar[0], S::TMA_BYTES_G);
+        mbar_arrive_expect_tx(&s_bar[1], S::TMA_BYTES - S::TMA_BYTES_G);
+        tma_load_3d(sG, &maps[3], xg, ci_lo - 1, S_GXX, &s_bar[0]);
+        tma_load_3d(sU, &maps[0], xa, da_lo, 0, &s_bar[1]);
+        tma_load_3d(sIE2, &maps[1], xa, da_lo, 0, &s_bar[1]);
+        tma_load_3d(sSeed, &maps[2], xs, ci_lo, S_DAX, &s_bar[1]);
         s_fail = 0;
-        if (!mbar_wait_bounded(&bar, 0u)) {
-          // record the timeout; let the copies land before the block leaves
+        if (!mbar_wait_bounded(&s_bar[0], 0u)) {
+          // record the timeout; let every copy land before the block leaves
           atomicOr(a.err, ERRFLAG_TIMEOUT);
-          mbar_wait_bounded(&bar, 0u);
+          mbar_wait_bounded(&s_bar[0], 0u);
+          mbar_wait_bounded(&s_bar[1], 0u);
           s_fail = 1;
         }
       }
       __syncthreads();
       if (s_fail) return;
       staged = true;
+      rest_pending = true;
     }
   }
   // Otherwise a tile whose windows lie inside the region, in maps whose rows
@@ -325,7 +333,13 @@ __device__ __forceinline__ void bwd_tile(const Args &a, const BwdRegion &rg, con
       sdU[1 * S::NC + r * S::NCJ + c] = uy;
     }
   }
+  if (rest_pending && tid == 0 && !mbar_wait_bounded(&s_bar[1], 0u)) {
+    atomicOr(a.err, ERRFLAG_TIMEOUT);
+    mbar_wait_bounded(&s_bar[1], 0u);
+    s_fail = 1;
+  }
   __syncthreads();
+  if (rest_pending && s_fail) return;
 
   // ---- du on the du region (in place over P' deps / 4) -----------------------
   const float q4 = 0.25f;
