@@ -27,7 +27,8 @@
  *     nothing written.  Launch failures return EPS_ERR_CUDA.  Device-side
  *     error flags are reported by eps_sync_status().
  *   * Calls on different streams are independent and may run concurrently
- *     when each has its own workspace.
+ *     when each has its own workspace (the pipelined part of multi-wave
+ *     eps_vjp calls runs on one library stream per device: see eps_vjp).
  */
 #ifndef EPSCHAIN_H
 #define EPSCHAIN_H
