@@ -16,6 +16,8 @@ and the scatter of the tile rows whose seed maps are complete.
 - Packed BF16 / FP16 fields on the same multi-wave shape (the packed
   contraction takes a column range too): against the oracle fed the
   decoded bytes, within the same tolerances.
+- The library's launch counter over one call of each form (what the bench
+  line's `gpu_launches` reports).
 """
 
 import numpy as np
@@ -176,3 +178,36 @@ def test_pipelined_packed_call_matches_the_oracle_on_decoded_fields(field_type):
     assert float(np.max(np.abs(g - ref)) / np.max(np.abs(ref))) <= 1e-4
     ref_e = orc.eps_hat(o, C)
     assert float(np.max(np.abs(e.cpu().numpy() - ref_e) / ref_e)) <= 1e-5
+
+
+def test_launch_counter_counts_each_form():
+    # eps_launch_count over one call: the one-wave form launches the
+    # contraction, the stencil and the scatter; a pipelined multi-wave call
+    # three contraction bands, the stencil, three seeds launches and up to
+    # three scatter launches; under per-kernel profiling the same call keeps
+    # the single-stream order (contraction, stencil, seeds, scatter)
+    import torch
+
+    import paper_2505_03352_gb300 as ec
+    small = ec.Problem(mx=64, my=48, nz=16, radius=3.0, beta=8.0)
+    shape = (3, small.nx, small.ny, small.nz)
+    EF = [_dev(synth.complex_field(shape, 9501))]
+    EA = [_dev(synth.complex_field(shape, 9502))]
+    C = _dev(synth.soi_layout(64, 48, 9503))
+    ec.eps_vjp(small, C, EF, EA)
+    torch.cuda.synchronize()
+    n0 = ec.eps_launch_count()
+    ec.eps_vjp(small, C, EF, EA)
+    assert ec.eps_launch_count() - n0 == 3
+    p, EF, EA, C1, _ = _case(nl=1, seed=9510)
+    ec.eps_vjp(p, C1, EF, EA)
+    torch.cuda.synchronize()
+    n0 = ec.eps_launch_count()
+    ec.eps_vjp(p, C1, EF, EA)
+    assert 8 <= ec.eps_launch_count() - n0 <= 10
+    ec.eps_profile_start()
+    n0 = ec.eps_launch_count()
+    ec.eps_vjp(p, C1, EF, EA)
+    assert ec.eps_launch_count() - n0 == 4
+    ec.eps_profile_stop(64)
+    ec.eps_sync_status()
