@@ -211,3 +211,25 @@ def test_launch_counter_counts_each_form():
     assert ec.eps_launch_count() - n0 == 4
     ec.eps_profile_stop(64)
     ec.eps_sync_status()
+
+
+@pytest.mark.parametrize("nz,nl", [(30, 2), (16, 16)],
+                         ids=["planes_not_a_multiple_of_4", "sixteen_wavelengths"])
+def test_pipelined_call_other_plane_counts_and_wavelengths(nz, nl):
+    # nz = 30: the stencil writes eps_hat column by column (no staging form
+    # takes it); 16 wavelengths: the contraction's largest map count
+    import paper_2505_03352_gb300 as ec
+    mx, my = 802, 722                 # 401 x 361 columns: ragged chunks and tiles
+    p = ec.Problem(mx=mx, my=my, nz=nz, radius=4.0, beta=16.0)
+    o = orc.Problem(mx=mx, my=my, nz=nz, radius=4.0, beta=16.0)
+    C = synth.soi_layout(mx, my, 9600 + nz)
+    shape = (3, p.nx, p.ny, nz)
+    EF = [synth.complex_field(shape, 9610 + l) for l in range(nl)]
+    EA = [synth.complex_field(shape, 9630 + l) for l in range(nl)]
+    g, e = ec.eps_vjp(p, _dev(C), [_dev(x) for x in EF], [_dev(x) for x in EA], eps_out=True)
+    ec.eps_sync_status()
+    ref_g = orc.vjp_fields(o, C, EF, EA)
+    ref_e = orc.eps_hat(o, C)
+    g, e = g.cpu().numpy(), e.cpu().numpy()
+    assert float(np.max(np.abs(g - ref_g)) / np.max(np.abs(ref_g))) <= 1e-4
+    assert float(np.max(np.abs(e - ref_e) / ref_e)) <= 1e-5
