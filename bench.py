@@ -46,6 +46,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 # the single-region contraction kernel and its copy/barrier helpers: a DRAM
 # traffic record is used only while this file is unchanged
 KERNEL_SOURCES = ["paper_2505_03352_gb300/csrc/epsc_contract_tma.cuh"]
+PACKED_KERNEL_SOURCES = ["paper_2505_03352_gb300/csrc/epsc_pack.cuh"]
 
 
 def parse():
@@ -210,9 +211,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ helpers
 
-def kernel_hash():
+def kernel_hash(sources=None):
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in (KERNEL_SOURCES if sources is None else sources):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -227,15 +228,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def committed_traffic(workload: str):
-    """dram read+write bytes per launch of the dominant kernel from the
-    committed ncu summary, if it was taken on the current kernel source."""
+def committed_traffic(workload: str, sources=None):
+    """dram read+write bytes per launch of the dominant kernel (or of the
+    kernel in `sources`) from the committed ncu summary, if it was taken on
+    the current kernel source."""
     if not os.path.exists(PROFILE_TRAFFIC):
         return None
     with open(PROFILE_TRAFFIC) as f:
         d = json.load(f)
     ent = d.get(workload)
-    if not ent or ent.get("kernel_hash") != kernel_hash():
+    if not ent or ent.get("kernel_hash") != kernel_hash(sources):
         return None
     return ent.get("bytes_per_launch")
 
@@ -900,7 +902,10 @@ def run_precision_variant(torch, ec, synth, dev, flush_l2, main):
                      "frac_of_copy_peak": (round(c_bytes / (c_ms * 1e-3) / 1e9 / peak, 4)
                                            if c_ms > 0 else None),
                      "algorithmic_frac": (round(c_alg / (c_ms * 1e-3) / 1e9 / peak, 4)
-                                          if c_ms > 0 else None)},
+                                          if c_ms > 0 else None),
+                     # ncu dram read + write bytes of one launch, committed
+                     # (null if the kernel changed since, or not captured)
+                     "traffic": committed_traffic(f"{w.name}_{name}", PACKED_KERNEL_SOURCES)},
                  "dJdC_max_dev_vs_fp32_path": (float((G - G32).abs().max()) / g32_max
                                                if g32_max > 0 else None),
                  "packed_bytes_per_field": ec.eps_packed_field_bytes(p, ft)}

@@ -35,12 +35,32 @@ def test_committed_traffic_needs_the_current_kernel_source(monkeypatch):
     w = synth.WORKLOADS[2]
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         rec = json.load(f)[w.name]
-    monkeypatch.setattr(bench, "kernel_hash", lambda: rec["kernel_hash"])
+    monkeypatch.setattr(bench, "kernel_hash", lambda sources=None: rec["kernel_hash"])
     assert bench.committed_traffic(w.name) == rec["bytes_per_launch"]
     assert rec["bytes_per_launch"] == rec["dram_read_bytes"] + rec["dram_write_bytes"]
-    monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "kernel_hash", lambda sources=None: "0" * 16)
     assert bench.committed_traffic(w.name) is None
     assert bench.committed_traffic("no such workload") is None
+
+
+def test_packed_traffic_record_is_keyed_by_the_packed_kernel_source(monkeypatch):
+    # the precision variant's record hashes the packed contraction's own
+    # source, not the FP32 contraction's
+    name = synth.WORKLOADS[5].name + "_bf16"
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)[name]
+    assert rec["kernel_files"] == bench.PACKED_KERNEL_SOURCES
+    assert rec["bytes_per_launch"] == rec["dram_read_bytes"] + rec["dram_write_bytes"]
+    seen = []
+
+    def fake_hash(sources=None):
+        seen.append(sources)
+        return rec["kernel_hash"] if sources == bench.PACKED_KERNEL_SOURCES else "0" * 16
+
+    monkeypatch.setattr(bench, "kernel_hash", fake_hash)
+    assert bench.committed_traffic(name, bench.PACKED_KERNEL_SOURCES) == rec["bytes_per_launch"]
+    assert bench.committed_traffic(name) is None
+    assert seen == [bench.PACKED_KERNEL_SOURCES, None]
 
 
 def test_measured_peak_is_the_driver_copy_rate():
